@@ -1,0 +1,237 @@
+/*
+ * sphnse.h -- C ABI of libsphnse: the pseudospectral quadrature method for the
+ * incompressible Navier-Stokes equations on the rotating unit sphere
+ * (Ganesh, Le Gia & Sloan), evaluated on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 2, Eq. (NSE_sphere)):  u_t + grad_u u - nu Delta u
+ *   + omega x u + grad p / rho = f,  div u = 0,  omega = 2 Omega cos(theta) xhat.
+ * Unknowns (Eq. (app_soln_rep)): u_N = sum_{L=1..N} sum_{|m|<=L} alpha_{L,m} Z_{L,m},
+ *   Z_{L,m} = lambda_L^{-1/2} Curl Y_{L,m}, lambda_L = L(L+1) (Eq. (stok_eig)).
+ * ODE system (Eq. (ode)): d alpha/dt = F(t, alpha),
+ *   F_{L,m} = fhat_{L,m} - nu lambda_L alpha_{L,m}
+ *             - ((zeta + 2 Omega cos theta) xhat x u, Z_{L,m})_M
+ *   with the discrete inner product of Eq. (disc_ip) on the Gauss-rectangle
+ *   rule Q_M of Eq. (quadrule): nlat = M/2 Gauss-Legendre latitudes x
+ *   nlon = M equispaced longitudes.  The vorticity/Coriolis product is the
+ *   non-gradient part of the nonlinear term (Eq. (short_nonlin1)) plus the
+ *   Coriolis operator (Eq. (C)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Packed coefficient vector: complex128 stored as interleaved (re, im)
+ *   doubles, m-major: index(m, L) = off[m] + L - max(m, 1) for m = 0..N and
+ *   L = max(m, 1)..N, off[0] = 0, off[m+1] = off[m] + N - max(m, 1) + 1;
+ *   n_coeff = (N+1)(N+2)/2 - 1 complex entries.  Only m >= 0 is stored;
+ *   alpha_{L,-m} = (-1)^m conj(alpha_{L,m}) and alpha_{L,0} is real.
+ * Y_{L,m} = Pt_L^m(cos theta) e^{i m phi} with the orthonormal associated
+ *   Legendre functions including the Condon-Shortley phase (Eq. (sph_har)).
+ * Grid arrays: row-major [nlat][nlon] doubles, latitude rows ordered north to
+ *   south (theta ascending), longitude phi_q = 2 pi q / nlon, q = 0..nlon-1.
+ * Memory: every pointer argument marked (device) is device memory owned by
+ *   the caller; the plan owns its tables and workspaces.  Calls are ordered
+ *   on the plan's stream (sphnse_set_stream) and do not synchronise the host,
+ *   except where a host output is documented (step info, norms).
+ * Errors: 0 on success, a negative SPHNSE_E_* code otherwise; inputs are not
+ *   modified on error.  Calls on one plan are not thread-safe.
+ */
+#ifndef SPHNSE_H
+#define SPHNSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SPHNSE_OK                  0
+#define SPHNSE_E_ARG              -1  /* bad argument: L < 1, nlon not even, nlat != nlon/2, nu < 0, NULL */
+#define SPHNSE_E_INEXACT          -2  /* nlon < 3L + 2: Q_M not exact on the Galerkin integrals (Eq. (M_choice)) */
+#define SPHNSE_E_NOMEM            -3  /* device or host allocation failed */
+#define SPHNSE_E_CUDA             -4  /* a CUDA runtime call failed */
+#define SPHNSE_E_NONFINITE        -5  /* a non-finite value appeared in the state or an input */
+#define SPHNSE_E_STEP_TOO_SMALL   -6  /* the adaptive step fell below 16 eps |t| */
+#define SPHNSE_E_TIMEOUT          -7  /* a bounded device wait ran out */
+#define SPHNSE_E_UNSUPPORTED      -8  /* nlon not of the form 2^a 3^b, or a precision not built */
+
+/* ---- plan parameters (sphnse_plan_set / sphnse_plan_get) ---------------- */
+#define SPHNSE_KEY_PRECISION       1  /* SPHNSE_FP64 | SPHNSE_FP32 | SPHNSE_BF16X3 (default FP64) */
+#define SPHNSE_KEY_NU              2  /* viscosity nu >= 0 */
+#define SPHNSE_KEY_OMEGA           3  /* rotation rate Omega */
+#define SPHNSE_KEY_RTOL            4  /* relative tolerance of sphnse_step (default 1e-6) */
+#define SPHNSE_KEY_ATOL            5  /* absolute tolerance of sphnse_step (default 1e-12) */
+#define SPHNSE_KEY_MAX_ORDER       6  /* highest NDF order, 1..5 (default 5) */
+#define SPHNSE_KEY_NEWTON_MAX_ITER 7  /* simplified-Newton iteration cap (default 4) */
+#define SPHNSE_KEY_H_MAX           8  /* largest step size (default 1) */
+#define SPHNSE_KEY_BDF             9  /* 1: kappa = 0 (BDF), 0: NDF (default) */
+#define SPHNSE_KEY_N_COEFF       100  /* read-only: n_coeff */
+#define SPHNSE_KEY_L             101  /* read-only: truncation degree */
+#define SPHNSE_KEY_NLAT          102  /* read-only */
+#define SPHNSE_KEY_NLON          103  /* read-only */
+#define SPHNSE_KEY_TABLE_BYTES   104  /* read-only: device bytes of Legendre tables held */
+
+#define SPHNSE_FP64    0  /* FP64 tables and arithmetic throughout */
+#define SPHNSE_FP32    1  /* FP32 tables, contractions, FFTs; FP64 state and update */
+#define SPHNSE_BF16X3  2  /* BF16 hi+lo split Legendre contractions on tcgen05 tensor
+                             cores with FP32 accumulation; FP32 FFTs; FP64 state */
+
+#define SPHNSE_MAXK 5     /* highest NDF order */
+
+typedef struct sphnse_plan sphnse_plan;
+
+/* Create a plan for truncation L on the nlat x nlon Gauss-rectangle grid.
+ * Computes in FP64 on the host the Gauss-Legendre nodes/weights and the
+ * orthonormal associated Legendre tables (Sec. 3 Eq. (quadrule); Sec. 4.2),
+ * and uploads them to the current CUDA device.  Requires nlon even,
+ * nlat == nlon/2, nlon >= 3L+2 (Eq. (M_choice)), nlon = 2^a 3^b.
+ * Returns NULL on error; sphnse_last_error() then gives the code. */
+sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Omega);
+
+/* Status of the last sphnse_plan_create on this thread. */
+int sphnse_last_error(void);
+
+/* Short text for a status code (static storage). */
+const char* sphnse_error_string(int code);
+
+/* Release the plan and its device memory (waits for its stream). NULL is ignored. */
+void sphnse_plan_destroy(sphnse_plan* plan);
+
+/* Set / read a plan parameter (SPHNSE_KEY_*).  Setting the precision builds
+ * the tables that precision needs (host FP64 master copy converted once). */
+int sphnse_plan_set(sphnse_plan* plan, int key, double value);
+int sphnse_plan_get(const sphnse_plan* plan, int key, double* value);
+
+/* Order all later work of the plan on this cudaStream_t (NULL: legacy default stream). */
+int sphnse_set_stream(sphnse_plan* plan, void* stream);
+
+/* Gauss-rectangle nodes: theta, cos(theta), sin(theta) and Gauss weights w_p
+ * (host arrays of nlat doubles each; any may be NULL).  Sec. 3, Eq. (quadrule). */
+int sphnse_grid_nodes(const sphnse_plan* plan, double* theta, double* x, double* sin_theta, double* w);
+
+/* ---- the right-hand side (the hot path) --------------------------------- */
+
+/* F = dalpha/dt of Eq. (ode) (Eqs. (app1_weak_form), (short_nonlin1), (C),
+ * (Coriolis_ZLm), Sec. 4.2):  dalpha_dt = forcing - nu lambda alpha
+ *   - ((zeta + 2 Omega cos theta) xhat x u, Z_{L,m})_M.
+ * alpha, forcing, dalpha_dt: (device) packed complex128, n_coeff entries;
+ * forcing may be NULL (zero).  t is accepted for the autonomous interface
+ * (the forcing is the caller's value at t).  alpha and dalpha_dt must not
+ * overlap.  Runs entirely on the device: coefficient prep, per-order Legendre
+ * synthesis, per-latitude inverse FFT + pointwise product + forward FFT,
+ * per-order Legendre analysis, recombination and diagonal update. */
+int sphnse_rhs(sphnse_plan* plan, double t, const double* alpha, const double* forcing,
+               double* dalpha_dt);
+
+/* Grid values of zeta = xhat.Curl_n u (Eq. (vort_app)), u_theta and u_phi
+ * for the field with coefficients alpha (Eq. (app_soln_rep)).
+ * alpha: (device) packed; zeta, u_theta, u_phi: (device) [nlat][nlon] doubles,
+ * any may be NULL. */
+int sphnse_grid_fields(sphnse_plan* plan, const double* alpha, double* zeta,
+                       double* u_theta, double* u_phi);
+
+/* Discrete projection of a tangential grid field onto Z_{L,m}
+ * (Eq. (disc_vec_orth_proj)): out_{L,m} = (v, Z_{L,m})_M.
+ * v_theta, v_phi: (device) [nlat][nlon]; out: (device) packed. */
+int sphnse_project(sphnse_plan* plan, const double* v_theta, const double* v_phi, double* out);
+
+/* ---- adaptive NDF time step (Sec. 4.2, Eq. (ode_disc)) ------------------ */
+
+typedef struct {
+    double* alpha;  /* (device) packed alpha_n, n_coeff complex; updated in place */
+    double* dif;    /* (device) (SPHNSE_MAXK + 2) x n_coeff complex backward differences */
+    double t;       /* current time t_n */
+    double h;       /* step size the next attempt starts from */
+    double t_end;   /* steps never pass t_end (use +inf for none) */
+    int    order;   /* current order k, 1..5 */
+    /* controller memory, set by sphnse_state_init; not for the caller */
+    int    nconhk;
+    int    havrate;
+    int    miter_k;
+    double h_dif;
+    double rate;
+    double miter_h;
+} sphnse_state;
+
+typedef struct {
+    double t;           /* time reached */
+    double h;           /* step size taken */
+    double err;         /* local error estimate of the accepted step (weighted max-norm) */
+    int    order;       /* order of the accepted step */
+    int    newton_iters;/* Newton iterations over all attempts */
+    int    rejections;  /* rejected attempts before acceptance */
+    int    rhs_evals;   /* F evaluations over all attempts */
+    int    next_order;  /* order chosen for the next step */
+    double next_h;      /* step size chosen for the next step */
+    double h_dif_before;/* step size the differences were expressed in before this step */
+} sphnse_step_info;
+
+/* Initialise an NDF state at (t0, alpha already in st->alpha): first
+ * difference D_0 = h0 F(t0, alpha0), order 1.  h0 <= 0 chooses
+ * h0 = min(h_max, sqrt(rtol) / (1.25 ||F / wt||_inf)).  forcing: (device) or NULL. */
+int sphnse_state_init(sphnse_plan* plan, sphnse_state* st, double t0, double h0,
+                      const double* forcing);
+
+/* One accepted step of the variable-order NDF integrator: predictor,
+ * simplified Newton on c F(alpha0 + d) - psi - d = 0 with the diagonal
+ * iteration matrix I - c J_d, J_d = -nu lambda + 2 i Omega m / lambda,
+ * local error estimate, step rejection and order/step selection (the
+ * MATLAB ODE-suite scheme the paper follows).  forcing: (device) steady over
+ * the step, or NULL.  Fills *info (host).  Synchronises the host once per
+ * Newton iteration to read four norms. */
+int sphnse_step(sphnse_plan* plan, sphnse_state* st, const double* forcing,
+                sphnse_step_info* info);
+
+/* One step with the step size h and order k fixed by the caller (frozen
+ * controller) and the corrector iterated until the Newton update is below
+ * 1e-15 in the weighted norm (at most newton_max iterations).  This is the
+ * map the adjoint differentiates. */
+int sphnse_replay_step(sphnse_plan* plan, sphnse_state* st, const double* forcing,
+                       double h, int k, int newton_max, sphnse_step_info* info);
+
+/* ---- adjoint (discretise-then-differentiate, frozen controller) --------- */
+
+/* out = J(alpha)^T w, J = dF/dalpha as a real-linear map of the packed real
+ * components.  alpha, w, out: (device) packed; out must not alias w.
+ * If nu_bar is not NULL, *nu_bar += <w, dF/dnu> = -<w, lambda alpha> (host). */
+int sphnse_rhs_adjoint(sphnse_plan* plan, const double* alpha, const double* w,
+                       double* out, double* nu_bar);
+
+/* Reverse of one sphnse_replay_step(h, k) taken from a state whose
+ * differences were expressed in step size h_dif_before, with alpha_next the
+ * state it produced.  abar (device, packed) and dbar (device,
+ * (SPHNSE_MAXK+2) x n_coeff complex) hold the adjoints of (alpha, dif) after
+ * the step on entry and before it on return; *nu_bar (host) is accumulated.
+ * The transposed corrector system (I - c J^T) mu = dbar_d is solved by
+ * fixed-point iteration preconditioned with (I - c J_d)^{-T}. */
+int sphnse_adjoint_step(sphnse_plan* plan, double h, int k, double h_dif_before,
+                        const double* alpha_next, double* abar, double* dbar,
+                        double* nu_bar);
+
+/* Reverse of sphnse_state_init: with D_0 = h0 F(alpha0), adds
+ * h0 J(alpha0)^T dbar_0 to abar and h0 <dbar_0, dF/dnu> to *nu_bar. */
+int sphnse_adjoint_init(sphnse_plan* plan, double h0, const double* alpha0,
+                        double* abar, const double* dbar, double* nu_bar);
+
+/* Final-time objective of a latitude band and a coefficient misfit:
+ * J = 1/2 sum over nodes with colatitude in [theta_lo, theta_hi] of
+ *     (2 pi / M) w_p |u|^2  +  sum_{all L,m} |alpha - target|^2,
+ * and its gradient with respect to the packed real components of alpha.
+ * alpha, target, grad: (device) packed; *J (host). */
+int sphnse_objective(sphnse_plan* plan, const double* alpha, const double* target,
+                     double theta_lo, double theta_hi, double* J, double* grad);
+
+/* ---- host-only helpers (no CUDA call; usable without a GPU) ------------- */
+
+/* Gauss-Legendre nodes and weights of the n-point rule the plan uses
+ * (Sec. 3, Eq. (quadrule)), nodes north to south: theta, cos(theta),
+ * sin(theta), w (host arrays of n doubles). */
+int sphnse_host_gauss_nodes(int n, double* theta, double* x, double* sin_theta, double* w);
+
+/* Orthonormal associated Legendre functions Pt_K^m(x_p), K = m..Kmax, at np
+ * nodes (Eq. (sph_har), Condon-Shortley phase): out[(K - m) * np + p] (host).
+ * sin_theta[p] = sqrt(1 - x[p]^2) supplied by the caller. */
+int sphnse_host_legendre(int Kmax, int m, int np, const double* x, const double* sin_theta,
+                         double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHNSE_H */

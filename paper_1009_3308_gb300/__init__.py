@@ -1,0 +1,193 @@
+"""GB300-native pseudospectral quadrature method for the Navier-Stokes
+equations on the rotating unit sphere (Ganesh, Le Gia & Sloan).
+
+Thin Python layer over the C ABI of ``libsphnse`` (include/sphnse.h):
+argument marshalling of PyTorch CUDA tensors and streams only.  Every step of
+the computation runs in the library's CUDA kernels; there is no CPU path.
+
+Coefficient vectors are complex128 CUDA tensors in the packed order
+(m = 0..L, then degree max(m,1)..L); grid arrays are float64 [nlat, nlon].
+"""
+import ctypes
+import math
+
+from . import _capi
+from ._capi import KEY, MAXK, PRECISION, SphnseError, State, StepInfo, check
+
+__all__ = ["Plan", "SphnseError", "PRECISION", "MAXK", "n_coeff"]
+
+
+def n_coeff(L):
+    return (L + 1) * (L + 2) // 2 - 1
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """One truncation degree L on the nlat x nlon Gauss-rectangle grid."""
+
+    def __init__(self, L, nlat, nlon, nu, Omega, precision="fp64", device=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsphnse runs on a CUDA device; none is available")
+        self.device = torch.device(device if device is not None else "cuda")
+        lib = _capi.lib()
+        with torch.cuda.device(self.device):
+            h = lib.sphnse_plan_create(int(L), int(nlat), int(nlon), float(nu), float(Omega))
+        if not h:
+            raise SphnseError("sphnse_plan_create", lib.sphnse_last_error())
+        self._h = ctypes.c_void_p(h)
+        self.L, self.nlat, self.nlon = int(L), int(nlat), int(nlon)
+        self.n_coeff = n_coeff(L)
+        self.set_precision(precision)
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.lib().sphnse_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- parameters -------------------------------------------------------
+    def set(self, key, value):
+        check("sphnse_plan_set", _capi.lib().sphnse_plan_set(self._h, KEY[key], float(value)))
+
+    def get(self, key):
+        v = ctypes.c_double()
+        check("sphnse_plan_get", _capi.lib().sphnse_plan_get(self._h, KEY[key], ctypes.byref(v)))
+        return v.value
+
+    def set_precision(self, precision):
+        self.set("PRECISION", PRECISION[precision])
+        self.precision = precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def nodes(self):
+        """(theta, x, sin_theta, w) as float64 CPU tensors."""
+        torch = _torch()
+        arrs = [torch.empty(self.nlat, dtype=torch.float64) for _ in range(4)]
+        ptrs = [ctypes.cast(a.data_ptr(), _capi.c_double_p) for a in arrs]
+        check("sphnse_grid_nodes", _capi.lib().sphnse_grid_nodes(self._h, *ptrs))
+        return tuple(arrs)
+
+    def _stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        check("sphnse_set_stream", _capi.lib().sphnse_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def _coeff(self, a, name):
+        torch = _torch()
+        if a is None:
+            return None
+        if a.dtype != torch.complex128 or not a.is_cuda or not a.is_contiguous() or a.numel() != self.n_coeff:
+            raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor of {self.n_coeff} entries")
+        return a
+
+    def empty_coeff(self):
+        torch = _torch()
+        return torch.empty(self.n_coeff, dtype=torch.complex128, device=self.device)
+
+    # -- hot path ---------------------------------------------------------
+    def rhs(self, alpha, forcing=None, out=None, t=0.0):
+        """F(t, alpha) of Eq. (ode)."""
+        alpha = self._coeff(alpha, "alpha")
+        forcing = self._coeff(forcing, "forcing")
+        out = self.empty_coeff() if out is None else self._coeff(out, "out")
+        self._stream()
+        check("sphnse_rhs", _capi.lib().sphnse_rhs(self._h, float(t), _ptr(alpha), _ptr(forcing), _ptr(out)))
+        return out
+
+    def grid_fields(self, alpha):
+        """(zeta, u_theta, u_phi) on the grid, float64 [nlat, nlon] CUDA tensors."""
+        torch = _torch()
+        alpha = self._coeff(alpha, "alpha")
+        outs = [torch.empty(self.nlat, self.nlon, dtype=torch.float64, device=self.device) for _ in range(3)]
+        self._stream()
+        check("sphnse_grid_fields", _capi.lib().sphnse_grid_fields(self._h, _ptr(alpha), *[_ptr(o) for o in outs]))
+        return tuple(outs)
+
+    def project(self, v_theta, v_phi, out=None):
+        """(v, Z_{L,m})_M for a tangential grid field."""
+        out = self.empty_coeff() if out is None else self._coeff(out, "out")
+        for v in (v_theta, v_phi):
+            if v.dtype != _torch().float64 or not v.is_contiguous() or v.shape != (self.nlat, self.nlon):
+                raise ValueError("grid fields must be contiguous float64 [nlat, nlon]")
+        self._stream()
+        check("sphnse_project", _capi.lib().sphnse_project(self._h, _ptr(v_theta), _ptr(v_phi), _ptr(out)))
+        return out
+
+    # -- adjoint ----------------------------------------------------------
+    def rhs_adjoint(self, alpha, w, out=None, want_nu=False):
+        """J(alpha)^T w (packed real components); with want_nu also <w, dF/dnu>."""
+        alpha = self._coeff(alpha, "alpha")
+        w = self._coeff(w, "w")
+        out = self.empty_coeff() if out is None else self._coeff(out, "out")
+        nb = ctypes.c_double(0.0)
+        self._stream()
+        check("sphnse_rhs_adjoint", _capi.lib().sphnse_rhs_adjoint(
+            self._h, _ptr(alpha), _ptr(w), _ptr(out), ctypes.byref(nb) if want_nu else None))
+        return (out, nb.value) if want_nu else out
+
+    def objective(self, alpha, target, theta_lo, theta_hi):
+        """(J, dJ/dalpha) of the band-energy + misfit objective."""
+        alpha = self._coeff(alpha, "alpha")
+        target = self._coeff(target, "target")
+        grad = self.empty_coeff()
+        J = ctypes.c_double()
+        self._stream()
+        check("sphnse_objective", _capi.lib().sphnse_objective(
+            self._h, _ptr(alpha), _ptr(target), float(theta_lo), float(theta_hi), ctypes.byref(J), _ptr(grad)))
+        return J.value, grad
+
+
+class Integrator:
+    """Adaptive NDF integrator state (sphnse_state) on a plan."""
+
+    def __init__(self, plan, alpha0, t0=0.0, h0=0.0, forcing=None, t_end=math.inf):
+        torch = _torch()
+        self.plan = plan
+        self.alpha = plan._coeff(alpha0, "alpha0").clone()
+        self.dif = torch.zeros((MAXK + 2, plan.n_coeff), dtype=torch.complex128, device=plan.device)
+        self.forcing = plan._coeff(forcing, "forcing")
+        self.st = State()
+        self.st.alpha = self.alpha.data_ptr()
+        self.st.dif = self.dif.data_ptr()
+        self.st.t_end = float(t_end)
+        plan._stream()
+        check("sphnse_state_init", _capi.lib().sphnse_state_init(
+            plan.handle, ctypes.byref(self.st), float(t0), float(h0), _ptr(self.forcing)))
+        self.h0 = self.st.h
+
+    @property
+    def t(self):
+        return self.st.t
+
+    def step(self):
+        info = StepInfo()
+        self.plan._stream()
+        check("sphnse_step", _capi.lib().sphnse_step(
+            self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), ctypes.byref(info)))
+        return info.as_dict()
+
+    def replay_step(self, h, k, newton_max=50):
+        info = StepInfo()
+        self.plan._stream()
+        check("sphnse_replay_step", _capi.lib().sphnse_replay_step(
+            self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), float(h), int(k), int(newton_max),
+            ctypes.byref(info)))
+        return info.as_dict()

@@ -1,0 +1,127 @@
+// Internal declarations of libsphnse (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/sphnse.h"
+
+namespace sph {
+
+// ---- index helpers --------------------------------------------------------
+// Packed coefficients: m-major, L = max(m,1)..N.
+__host__ __device__ inline int packed_off(int N, int m) {
+    return m == 0 ? 0 : N + (m - 1) * (N + 1) - (m - 1) * m / 2;
+}
+__host__ __device__ inline int packed_index(int N, int m, int L) {
+    return packed_off(N, m) + L - (m > 0 ? m : 1);
+}
+inline int n_packed(int N) { return (N + 1) * (N + 2) / 2 - 1; }
+
+// Extended-degree ("ext") rows: for each m the degrees K = m..N+1 (n_m = N+2-m
+// of them), split by the parity of K - m: even rows first (K = m + 2j,
+// j < ne(m)), then odd rows (K = m + 1 + 2j, j < no(m)).  Degree N+1 is needed
+// by the theta-derivative recombination.
+__host__ __device__ inline int ext_off(int N, int m) { return m * (N + 2) - m * (m - 1) / 2; }
+__host__ __device__ inline int ext_count(int N, int m) { return N + 2 - m; }
+__host__ __device__ inline int ext_even(int N, int m) { return (N + 3 - m) / 2; }
+__host__ __device__ inline int ext_odd(int N, int m) { return (N + 2 - m) / 2; }
+__host__ __device__ inline int ext_row(int N, int m, int K) {
+    int d = K - m;
+    return ext_off(N, m) + ((d & 1) ? ext_even(N, m) + (d >> 1) : (d >> 1));
+}
+inline int n_ext(int N) { return ext_off(N, N + 1); }
+
+// ---- host precompute (host_tables.cpp) ------------------------------------
+// Gauss-Legendre rule, nodes north to south: theta, cos, sin, weights.
+void gauss_legendre(int n, double* theta, double* x, double* s, double* w);
+// Orthonormal associated Legendre functions Pt_K^m(x_p), K = m..Kmax, for
+// the np given nodes; out[(K - m) * np + p].  Extended binary exponent inside.
+void legendre_column(int Kmax, int m, int np, const double* x, const double* s, double* out);
+// Full table in the synthesis layout: out[ext_row(N, m, K) * nh + p] for the nh
+// northern nodes (FP64), computed with nthreads host threads.
+void legendre_table_syn(int N, int nh, const double* x, const double* s, double* out);
+
+// ---- radix plan of the longitude FFT (2^a 3^b) -----------------------------
+struct FFTPlan {
+    int n = 0;
+    int nstages = 0;
+    int radix[24];
+};
+bool make_fft_plan(int n, FFTPlan* p);
+
+// ---- device tables ----------------------------------------------------------
+struct Tables {
+    void* syn = nullptr;     // [n_ext][nh]: rows of Pt over northern nodes (synthesis)
+    void* ana = nullptr;     // per (m, parity) block [nh][rows] (analysis)
+    void* syn_lo = nullptr;  // BF16X3: low parts
+    void* ana_lo = nullptr;
+    size_t bytes = 0;
+    bool built = false;
+};
+
+}  // namespace sph
+
+struct sphnse_plan {
+    int N = 0, nlat = 0, nlon = 0, nh = 0;   // nh = ceil(nlat/2) northern rows
+    double nu = 0, Omega = 0;
+    int precision = SPHNSE_FP64;
+    double rtol = 1e-6, atol = 1e-12, h_max = 1.0;
+    int max_order = 5, newton_max = 4, bdf = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_coeff = 0, n_ext = 0;
+    sph::FFTPlan fft;
+
+    std::vector<double> theta, x, s, w;   // host nodes
+    std::vector<double> psyn_host;        // FP64 master table, synthesis layout
+
+    // device constants
+    double* d_x = nullptr;       // cos(theta_p), nlat
+    double* d_s = nullptr;       // sin(theta_p), nlat
+    double* d_rw = nullptr;      // (2 pi / M) w_p / sin(theta_p), nlat
+    double* d_tw = nullptr;      // e^{-2 pi i t / M}, M complex (FP64)
+    float* d_tw32 = nullptr;     // same in FP32
+    int2* d_lm = nullptr;        // (L, m) of each packed entry
+
+    sph::Tables tab[3];
+
+    // workspaces (sized for the largest field counts: 5 synthesis, 3 analysis)
+    void* d_bsyn = nullptr;      // [n_ext][2 * 5] (re, im) per field, precision type
+    void* d_gsyn = nullptr;      // [5][nlat][N+1] complex
+    void* d_gana = nullptr;      // [3][nlat][N+1] complex
+    void* d_hana = nullptr;      // [n_ext][2 * 3]
+    double* d_work = nullptr;    // NDF / adjoint vectors: 8 x n_coeff complex
+    double* d_tmp = nullptr;     // 2 x n_coeff complex scratch for F / J^T w
+    unsigned long long* d_norms = nullptr;  // 8 reduction slots
+    double* h_norms = nullptr;   // pinned host mirror
+    size_t work_bytes = 0;
+};
+
+namespace sph {
+
+// ---- launchers (kernels in *.cu) ------------------------------------------
+enum RingMode { RING_RHS = 0, RING_GRID = 1, RING_PROJECT = 2, RING_ADJOINT = 3 };
+
+// prep: coefficient sets for synthesis.  nsets fields from alpha (3: zeta,
+// theta, phi) and optionally 2 more (theta, phi) from beta scaled by 1/s_m.
+int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int prec);
+int launch_synthesis(sphnse_plan* P, int nfields, int prec);
+int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const double* gin1,
+                double* gout0, double* gout1, double* gout2);
+int launch_analysis(sphnse_plan* P, int nfields, int prec);
+// finish: kind 0 = RHS (F = f - nu lam alpha - N), 1 = projection (N),
+// 2 = adjoint (out = -nu lam w - s_m (N_X + lam^{1/2} H_rho))
+int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha,
+                  const double* forcing, double* out);
+
+int ensure_tables(sphnse_plan* P, int prec);
+int check_cuda(cudaError_t e);
+
+// whole pipelines
+int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, double* out);
+int rhs_adjoint_device(sphnse_plan* P, const double* alpha, const double* w, double* out);
+
+}  // namespace sph

@@ -1,0 +1,304 @@
+// Spectral-side kernels of the RHS F (Eq. (ode)) on CUDA cores:
+//   prep       coefficient sets for synthesis (Eqs. (stok_eig), (vort_app))
+//   synthesis  per-order Legendre sums over the northern nodes, even/odd
+//              split (north = E + O, south = E - O)
+//   analysis   per-order Legendre sums of the quadrature-weighted Fourier
+//              profiles (Eq. (disc_vec_orth_proj))
+//   finish     degree-shift recombination and the diagonal Stokes update
+//              (Sec. 4.2: nu lambda_L alpha_{L,m}) plus forcing.
+// Templated on the contraction type T (double for SPHNSE_FP64, float for
+// SPHNSE_FP32); the coefficient state in and out is always FP64.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace sph {
+
+__device__ __forceinline__ double eps_lm(int L, int m) {
+    if (L <= m) return 0.0;
+    double a = double(L) * L - double(m) * m;
+    return sqrt(a / (4.0 * L * L - 1.0));
+}
+
+// ---------------------------------------------------------------------------
+// prep: one thread per ext row (m, K), K = m..N+1.
+//   field 0 (zeta):  lambda_K^{1/2} alpha_K
+//   field 1 (theta): a_K = lambda_K^{-1/2} alpha_K
+//   field 2 (phi):   (K-1) eps_{K,m} a_{K-1} - (K+2) eps_{K+1,m} a_{K+1}
+// (sin(theta) d/dtheta Pt_L^m = L eps_{L+1,m} Pt_{L+1}^m - (L+1) eps_{L,m} Pt_{L-1}^m
+//  regrouped by degree).  With beta (adjoint): fields 3, 4 are the theta/phi
+// sets of beta / s_m, s_m = 1 (m = 0) or 2.
+template <typename T>
+__global__ void k_prep(const double2* __restrict__ alpha, const double2* __restrict__ beta,
+                       T* __restrict__ bsyn, int N, int nf) {
+    const int m = blockIdx.y;
+    const int K = m + blockIdx.x * blockDim.x + threadIdx.x;
+    if (K > N + 1) return;
+    const int lo = m > 0 ? m : 1;
+    auto a_of = [&](const double2* v, int Kp, double scale) -> double2 {
+        if (Kp < lo || Kp > N) return make_double2(0.0, 0.0);
+        double2 c = v[packed_index(N, m, Kp)];
+        double f = scale / sqrt(double(Kp) * (Kp + 1.0));
+        return make_double2(c.x * f, c.y * f);
+    };
+    T* out = bsyn + size_t(ext_row(N, m, K)) * (2 * nf);
+    // zeta
+    if (K >= lo && K <= N) {
+        double2 c = alpha[packed_index(N, m, K)];
+        double f = sqrt(double(K) * (K + 1.0));
+        out[0] = T(c.x * f);
+        out[1] = T(c.y * f);
+    } else {
+        out[0] = T(0);
+        out[1] = T(0);
+    }
+    const double cu = (K - 1) * eps_lm(K, m), cd = (K + 2) * eps_lm(K + 1, m);
+    {
+        double2 aK = a_of(alpha, K, 1.0), am = a_of(alpha, K - 1, 1.0), ap = a_of(alpha, K + 1, 1.0);
+        out[2] = T(aK.x);
+        out[3] = T(aK.y);
+        out[4] = T(cu * am.x - cd * ap.x);
+        out[5] = T(cu * am.y - cd * ap.y);
+    }
+    if (nf == 5) {
+        const double sc = m == 0 ? 1.0 : 0.5;
+        double2 aK = a_of(beta, K, sc), am = a_of(beta, K - 1, sc), ap = a_of(beta, K + 1, sc);
+        out[6] = T(aK.x);
+        out[7] = T(aK.y);
+        out[8] = T(cu * am.x - cd * ap.x);
+        out[9] = T(cu * am.y - cd * ap.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// synthesis: block (p-tile, m); thread = one northern node p.
+//   g_f(theta_p) = sum_K Pt_K^m(x_p) b_{f,K}: even rows E, odd rows O;
+//   north row p: E + O, south row nlat-1-p: E - O.
+// Field scalings: theta fields (i m / sin), phi fields (-1 / sin), zeta none.
+// Output gsyn[f][row][m] complex.
+template <typename T, int NF>
+__global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, const T* __restrict__ bsyn,
+                                                    T* __restrict__ gsyn, const double* __restrict__ sinth,
+                                                    int N, int nh, int nlat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* B = reinterpret_cast<T*>(smem_raw);
+    const int m = blockIdx.y;
+    const int e0 = ext_off(N, m), cnt = ext_count(N, m), ne = ext_even(N, m), no = ext_odd(N, m);
+    for (int i = threadIdx.x; i < cnt * 2 * NF; i += blockDim.x) B[i] = bsyn[size_t(e0) * 2 * NF + i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nh) return;
+    T ev[2 * NF], od[2 * NF];
+#pragma unroll
+    for (int f = 0; f < 2 * NF; ++f) { ev[f] = T(0); od[f] = T(0); }
+    const T* Pe = psyn + size_t(e0) * nh + p;
+#pragma unroll 4
+    for (int j = 0; j < ne; ++j) {
+        const T pv = __ldg(Pe + size_t(j) * nh);
+        const T* b = B + j * 2 * NF;
+#pragma unroll
+        for (int f = 0; f < 2 * NF; ++f) ev[f] = fma(pv, b[f], ev[f]);
+    }
+    const T* Po = psyn + size_t(e0 + ne) * nh + p;
+#pragma unroll 4
+    for (int j = 0; j < no; ++j) {
+        const T pv = __ldg(Po + size_t(j) * nh);
+        const T* b = B + (ne + j) * 2 * NF;
+#pragma unroll
+        for (int f = 0; f < 2 * NF; ++f) od[f] = fma(pv, b[f], od[f]);
+    }
+    const T inv_s = T(1.0 / sinth[p]);
+    const T mm = T(m);
+    const size_t ld = size_t(N + 1);
+#pragma unroll
+    for (int hemi = 0; hemi < 2; ++hemi) {
+        const int row = hemi == 0 ? p : nlat - 1 - p;
+        if (hemi == 1 && row == p) break;  // equator of an odd grid
+        const T sg = hemi == 0 ? T(1) : T(-1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T gr = ev[2 * f] + sg * od[2 * f];
+            T gi = ev[2 * f + 1] + sg * od[2 * f + 1];
+            T outr, outi;
+            if (f == 0) {
+                outr = gr; outi = gi;
+            } else if (f == 1 || f == 3) {  // (i m / sin) g
+                outr = -mm * gi * inv_s;
+                outi = mm * gr * inv_s;
+            } else {                         // -(1 / sin) g
+                outr = -gr * inv_s;
+                outi = -gi * inv_s;
+            }
+            T* dst = gsyn + ((size_t(f) * nlat + row) * ld + m) * 2;
+            dst[0] = outr;
+            dst[1] = outi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// analysis: block (j-tile, m, parity); thread = one ext row (degree K).
+//   H_{f,K} = sum_{north p} Pt_K^m(x_p) [G_f(p) + (-1)^{K+m} G_f(p')],
+// p' the mirror row; the table block is [nh][rows] so that threads of a warp
+// read consecutive degrees.  G already carries (2 pi / M) w_p / sin(theta_p)
+// (and sin(theta_p) for the scalar adjoint field).
+template <typename T, int NF>
+__global__ void __launch_bounds__(128) k_analysis(const T* __restrict__ pana, const T* __restrict__ gana,
+                                                   T* __restrict__ hana, int N, int nh, int nlat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);  // [nh][2 NF]
+    const int m = blockIdx.y, par = blockIdx.z;
+    const int ne = ext_even(N, m), no = ext_odd(N, m);
+    const int nrows = par ? no : ne;
+    if (int(blockIdx.x * blockDim.x) >= nrows) return;
+    const int rowstart = ext_off(N, m) + (par ? ne : 0);
+    const size_t ld = size_t(N + 1);
+    for (int i = threadIdx.x; i < nh * NF; i += blockDim.x) {
+        const int p = i / NF, f = i % NF;
+        const int pr = nlat - 1 - p;
+        const T* a = gana + ((size_t(f) * nlat + p) * ld + m) * 2;
+        T ar = a[0], ai = a[1], br = T(0), bi = T(0);
+        if (pr != p) {
+            const T* b = gana + ((size_t(f) * nlat + pr) * ld + m) * 2;
+            br = b[0];
+            bi = b[1];
+        }
+        S[p * 2 * NF + 2 * f] = par ? ar - br : ar + br;
+        S[p * 2 * NF + 2 * f + 1] = par ? ai - bi : ai + bi;
+    }
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nrows) return;
+    T acc[2 * NF];
+#pragma unroll
+    for (int f = 0; f < 2 * NF; ++f) acc[f] = T(0);
+    const T* Pa = pana + size_t(rowstart) * nh + j;
+#pragma unroll 4
+    for (int p = 0; p < nh; ++p) {
+        const T pv = __ldg(Pa + size_t(p) * nrows);
+        const T* sp = S + p * 2 * NF;
+#pragma unroll
+        for (int f = 0; f < 2 * NF; ++f) acc[f] = fma(pv, sp[f], acc[f]);
+    }
+    T* dst = hana + size_t(rowstart + j) * 2 * NF;
+#pragma unroll
+    for (int f = 0; f < 2 * NF; ++f) dst[f] = acc[f];
+}
+
+// ---------------------------------------------------------------------------
+// finish: one thread per packed (L, m).
+//   N_{L,m} = lambda^{-1/2} [ -i m H^theta_L
+//             - (L eps_{L+1,m} H^phi_{L+1} - (L+1) eps_{L,m} H^phi_{L-1}) ]
+// kind 0: out = forcing - nu lambda alpha - N              (Eq. (ode))
+// kind 1: out = N                                          (projection)
+// kind 2: out = -nu lambda w - s_m (N + lambda^{1/2} H^rho_L)  (J^T w; alpha = w)
+template <typename T>
+__global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const double2* __restrict__ alpha,
+                         const double2* __restrict__ forcing, double2* __restrict__ out,
+                         const int2* __restrict__ lm, int N, double nu, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = lm[i].x, m = lm[i].y;
+    const double lam = double(L) * (L + 1.0);
+    const double isl = 1.0 / sqrt(lam);
+    const T* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
+    const T* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
+    const double htr = double(hL[0]), hti = double(hL[1]);
+    const double hur = double(hU[2]), hui = double(hU[3]);
+    double hdr = 0.0, hdi = 0.0;
+    if (L - 1 >= m) {
+        const T* hD = hana + size_t(ext_row(N, m, L - 1)) * 2 * nf;
+        hdr = double(hD[2]);
+        hdi = double(hD[3]);
+    }
+    const double eu = L * eps_lm(L + 1, m), ed = (L + 1) * eps_lm(L, m);
+    const double nr = isl * (m * hti - (eu * hur - ed * hdr));
+    const double ni = isl * (-m * htr - (eu * hui - ed * hdi));
+    double2 r;
+    if (kind == 0) {
+        const double2 a = alpha[i];
+        double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
+        r.x = f.x - nu * lam * a.x - nr;
+        r.y = f.y - nu * lam * a.y - ni;
+    } else if (kind == 1) {
+        r = make_double2(nr, ni);
+    } else {
+        const double2 wv = alpha[i];
+        const double sm = m == 0 ? 1.0 : 2.0;
+        const double sl = sqrt(lam);
+        r.x = -nu * lam * wv.x - sm * (nr + sl * double(hL[4]));
+        r.y = -nu * lam * wv.y - sm * (ni + sl * double(hL[5]));
+    }
+    out[i] = r;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+template <typename T>
+static int prep_t(sphnse_plan* P, const double* alpha, const double* beta) {
+    const int nf = beta ? 5 : 3;
+    dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1);
+    k_prep<T><<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
+                                           reinterpret_cast<const double2*>(beta),
+                                           reinterpret_cast<T*>(P->d_bsyn), P->N, nf);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int prec) {
+    return prec == SPHNSE_FP64 ? prep_t<double>(P, alpha, beta) : prep_t<float>(P, alpha, beta);
+}
+
+template <typename T, int NF>
+static int synth_t(sphnse_plan* P) {
+    dim3 blk(128), grd((P->nh + 127) / 128, P->N + 1);
+    size_t sm = size_t(P->N + 2) * 2 * NF * sizeof(T);
+    k_synthesis<T, NF><<<grd, blk, sm, P->stream>>>(
+        reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
+        reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn), P->d_s, P->N, P->nh, P->nlat);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_synthesis(sphnse_plan* P, int nfields, int prec) {
+    if (prec == SPHNSE_FP64) return nfields == 5 ? synth_t<double, 5>(P) : synth_t<double, 3>(P);
+    return nfields == 5 ? synth_t<float, 5>(P) : synth_t<float, 3>(P);
+}
+
+template <typename T, int NF>
+static int anal_t(sphnse_plan* P) {
+    const int maxrows = ext_even(P->N, 0);
+    dim3 blk(128), grd((maxrows + 127) / 128, P->N + 1, 2);
+    size_t sm = size_t(P->nh) * 2 * NF * sizeof(T);
+    if (sm > 48 * 1024) {
+        cudaFuncSetAttribute(k_analysis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    }
+    k_analysis<T, NF><<<grd, blk, sm, P->stream>>>(
+        reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].ana),
+        reinterpret_cast<const T*>(P->d_gana), reinterpret_cast<T*>(P->d_hana), P->N, P->nh, P->nlat);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_analysis(sphnse_plan* P, int nfields, int prec) {
+    if (prec == SPHNSE_FP64) return nfields == 3 ? anal_t<double, 3>(P) : anal_t<double, 2>(P);
+    return nfields == 3 ? anal_t<float, 3>(P) : anal_t<float, 2>(P);
+}
+
+int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const double* forcing,
+                  double* out) {
+    const int n = P->n_coeff;
+    const int nf = kind == 2 ? 3 : 2;
+    dim3 blk(256), grd((n + 255) / 256);
+    if (prec == SPHNSE_FP64)
+        k_finish<double><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const double*>(P->d_hana), nf,
+                                                     reinterpret_cast<const double2*>(alpha),
+                                                     reinterpret_cast<const double2*>(forcing),
+                                                     reinterpret_cast<double2*>(out), P->d_lm, P->N, P->nu, n);
+    else
+        k_finish<float><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const float*>(P->d_hana), nf,
+                                                    reinterpret_cast<const double2*>(alpha),
+                                                    reinterpret_cast<const double2*>(forcing),
+                                                    reinterpret_cast<double2*>(out), P->d_lm, P->N, P->nu, n);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace sph
