@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the RHS evaluation F(t, alpha) of the pseudospectral
+quadrature method (rotating-sphere Navier-Stokes) at truncation L = 511 on
+the 768 x 1536 Gauss-rectangle grid, mixed precision.
+
+One step = one RHS evaluation (coefficient prep, per-order Legendre
+synthesis, per-latitude FFT + product + FFT, per-order Legendre analysis,
+recombination and diagonal update) on device-resident synthetic inputs.
+The Legendre tables (>= 200 MB) exceed the 129 MB L2, so every step streams
+them from HBM; no extra L2 flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the single
+RHS does not shard without an all-to-all; replicas only) and rank 0 prints
+the whole-job aggregate.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS evals/s at L=511 (768x1536 grid), mixed precision"
+UNIT = "RHS/s"
+WORKLOAD = "L511"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, help="fp32 | bf16x3 (default: best mixed path)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def result(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except Exception:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inside = [r for r in rows if self.t0 - 1 <= r[0] <= self.t1 + 1] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes / flops of the kernels (per launch)
+
+def sizes(L, nlat):
+    nh = (nlat + 1) // 2
+    n_ext = (L + 2) * (L + 3) // 2 - 1
+    return nh, n_ext, nh * n_ext
+
+
+def algorithmic(stage, L, nlat, prec):
+    """(bytes, flops) one launch of a stage must move / execute at minimum."""
+    nh, n_ext, E = sizes(L, nlat)
+    tb = {"fp64": 8, "fp32": 4, "bf16x3": 4}[prec]     # table bytes per entry (hi+lo for bf16)
+    vb = 8 if prec == "fp64" else 4                     # intermediate real size
+    g = nlat * (L + 1) * 2 * vb                         # one complex [nlat][L+1] field
+    if stage == "synthesis":
+        return E * tb + n_ext * 6 * vb + 3 * g, 12 * E
+    if stage == "analysis":
+        return E * tb + 2 * g + n_ext * 4 * vb, 8 * E
+    if stage == "ring":
+        return 5 * g, 0
+    return 0, 0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """Bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return e["bytes_per_launch"] if h == e["source_sha"] else None
+
+
+# --------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_rhs(plan, a, out, steps, torch):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        plan.rhs(a, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline(w, target_s=15.0):
+    """The FP64 oracle as it stands, on this host's cores: RHS evaluations at
+    the benchmark workload (tables built first, not timed)."""
+    from oracle.rhs import Problem, rhs_separable
+    c = w["config"]
+    prob = Problem(c["L"], c["nlon"], c["nu"], c["Omega"])
+    prob.tables()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        rhs_separable(prob, w["alpha0"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or n >= 50:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full RHS evaluations at L=511 on 768x1536 (FP64 numpy oracle; "
+                      f"Legendre tables built before timing), {el:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.rhs import Problem, rhs_separable
+    from seeded_inputs import workload
+    w = workload(WORKLOAD)
+    c = w["config"]
+    prob = Problem(c["L"], c["nlon"], c["nu"], c["Omega"])
+    prob.tables()
+    # each step is one full oracle RHS (~2 s); the count is capped so that the
+    # run stays within a few minutes
+    steps = max(1, min(args.steps, 40))
+    warm = max(0, min(args.warmup, 2))
+    for _ in range(warm):
+        rhs_separable(prob, w["alpha0"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rhs_separable(prob, w["alpha0"])
+    el = time.perf_counter() - t0
+    v = steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "L=511 RHS, 768x1536 Gauss-rectangle grid, FP64 CPU oracle",
+                       "L": 511, "nlat": 768, "nlon": 1536},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{steps} full RHS evaluations at L=511 (numpy FP64 oracle)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1009_3308_gb300 import Plan, _capi
+    from seeded_inputs import workload
+
+    world, rank, local = dist_setup(args)
+    w = workload(WORKLOAD)
+    c = w["config"]
+    L, nlat, nlon = c["L"], c["nlat"], c["nlon"]
+    prec = args.precision or _best_mixed()
+    plan = Plan(L, nlat, nlon, c["nu"], c["Omega"], precision=prec)
+    a = torch.from_numpy(w["alpha0"]).cuda()
+    out = plan.empty_coeff()
+    lib = _capi.lib()
+
+    for _ in range(max(args.warmup, 3)):
+        plan.rhs(a, out=out)
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    lib.sphnse_stage_timing(plan.handle, 1)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.mark_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.rhs(a, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk.mark_end()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(world, ms_total)
+    import ctypes
+    st_ms = (ctypes.c_double * 7)()
+    st_n = (ctypes.c_long * 7)()
+    lib.sphnse_stage_times(plan.handle, st_ms, st_n)
+    lib.sphnse_stage_timing(plan.handle, 0)
+    clocks = clk.result()
+    stage = {name: {"ms": st_ms[i], "launches": st_n[i]} for i, name in enumerate(_capi.STAGES)}
+    launches = int(sum(st_n[i] for i in range(7)))
+
+    value = world * args.steps / (ms_total / 1e3)
+    ms_per_step = ms_total / args.steps
+
+    # dominant kernel and its roofline (live durations from the timed region)
+    dom = max(("synthesis", "analysis", "ring"), key=lambda k: stage[k]["ms"])
+    avg_ms = stage[dom]["ms"] / max(stage[dom]["launches"], 1)
+    nbytes, _ = algorithmic(dom, L, nlat, prec)
+    peak, peak_kind = peaks()
+    achieved = nbytes / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes": nbytes,
+                "avg_launch_ms": avg_ms, "traffic": ncu_traffic(f"{dom}:{prec}:L511")}
+
+    # end to end through the public API with host buffers
+    pin_in = torch.from_numpy(w["alpha0"]).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    dev_in = torch.empty_like(a)
+    for _ in range(3):
+        dev_in.copy_(pin_in, non_blocking=True)
+        plan.rhs(dev_in, out=out)
+        pin_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    k_e2e = min(args.steps, 1000)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        dev_in.copy_(pin_in, non_blocking=True)
+        plan.rhs(dev_in, out=out)
+        pin_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    el = time.perf_counter() - t0
+    el = max_over_ranks(world, el)
+    e2e = {"value": world * k_e2e / el, "unit": UNIT, "h2d_bytes_per_step": pin_in.numel() * 16,
+           "d2h_bytes_per_step": pin_out.numel() * 16, "steps": k_e2e}
+
+    extras = {}
+    if not args.no_extras:
+        ref = None
+        for p2 in ("fp64", "fp32", "bf16x3"):
+            if p2 == prec or (p2 == "bf16x3" and not _has_bf16x3()):
+                continue
+            plan.set_precision(p2)
+            ms = time_rhs(plan, a, out, min(args.steps, 200 if p2 == "fp64" else 1000), torch)
+            extras[p2] = {"rhs_per_s": 1e3 / ms, "ms_per_rhs": ms}
+        # accuracy of the timed path against the FP64 GPU path at full size
+        plan.set_precision("fp64")
+        f64 = plan.rhs(a).cpu().numpy()
+        plan.set_precision(prec)
+        fm = plan.rhs(a).cpu().numpy()
+        extras["rel_err_vs_fp64"] = float(np.linalg.norm(fm - f64) / np.linalg.norm(f64))
+        if "fp64" in extras:
+            extras["speedup_vs_fp64"] = value / world / extras["fp64"]["rhs_per_s"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32acc", "fp64": "f64"}[prec],
+                "data": "synthetic",
+                "config": {"workload": "L=511 RHS evaluation, 768x1536 Gauss-rectangle grid, "
+                                       "seeded spectrum exp(-0.02 L)/(L(L+1)), nu=5e-5, Omega=1",
+                           "L": L, "nlat": nlat, "nlon": nlon, "precision": prec,
+                           "l2": "inputs larger than L2 (Legendre tables streamed every step)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "stages_ms": {k: v["ms"] for k, v in stage.items()}, **extras}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _has_bf16x3():
+    return os.environ.get("SPHNSE_BENCH_BF16X3", "1") == "1" and _bf16_ready()
+
+
+def _bf16_ready():
+    try:
+        from paper_1009_3308_gb300 import _capi
+        return bool(getattr(_capi, "BF16X3_READY", False))
+    except Exception:
+        return False
+
+
+def _best_mixed():
+    return "bf16x3" if _bf16_ready() else "fp32"
+
+
+if __name__ == "__main__":
+    main()

@@ -50,7 +50,7 @@ extern "C" {
 #define SPHNSE_E_NONFINITE        -5  /* a non-finite value appeared in the state or an input */
 #define SPHNSE_E_STEP_TOO_SMALL   -6  /* the adaptive step fell below 16 eps |t| */
 #define SPHNSE_E_TIMEOUT          -7  /* a bounded device wait ran out */
-#define SPHNSE_E_UNSUPPORTED      -8  /* nlon not of the form 2^a 3^b, or a precision not built */
+#define SPHNSE_E_UNSUPPORTED      -8  /* nlon not 2^a 3^b or above 1536, or a precision not built */
 
 /* ---- plan parameters (sphnse_plan_set / sphnse_plan_get) ---------------- */
 #define SPHNSE_KEY_PRECISION       1  /* SPHNSE_FP64 | SPHNSE_FP32 | SPHNSE_BF16X3 (default FP64) */
@@ -77,11 +77,12 @@ extern "C" {
 
 typedef struct sphnse_plan sphnse_plan;
 
+
 /* Create a plan for truncation L on the nlat x nlon Gauss-rectangle grid.
  * Computes in FP64 on the host the Gauss-Legendre nodes/weights and the
  * orthonormal associated Legendre tables (Sec. 3 Eq. (quadrule); Sec. 4.2),
  * and uploads them to the current CUDA device.  Requires nlon even,
- * nlat == nlon/2, nlon >= 3L+2 (Eq. (M_choice)), nlon = 2^a 3^b.
+ * nlat == nlon/2, nlon >= 3L+2 (Eq. (M_choice)), nlon = 2^a 3^b <= 1536.
  * Returns NULL on error; sphnse_last_error() then gives the code. */
 sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Omega);
 
@@ -101,6 +102,11 @@ int sphnse_plan_get(const sphnse_plan* plan, int key, double* value);
 
 /* Order all later work of the plan on this cudaStream_t (NULL: legacy default stream). */
 int sphnse_set_stream(sphnse_plan* plan, void* stream);
+
+/* Wait for the plan's stream.  Returns SPHNSE_E_TIMEOUT if a kernel of the
+ * plan gave up a bounded wait since the last call (the status is cleared),
+ * SPHNSE_E_CUDA on a CUDA error. */
+int sphnse_sync(sphnse_plan* plan);
 
 /* Gauss-rectangle nodes: theta, cos(theta), sin(theta) and Gauss weights w_p
  * (host arrays of nlat doubles each; any may be NULL).  Sec. 3, Eq. (quadrule). */
@@ -217,6 +223,27 @@ int sphnse_adjoint_init(sphnse_plan* plan, double h0, const double* alpha0,
  * alpha, target, grad: (device) packed; *J (host). */
 int sphnse_objective(sphnse_plan* plan, const double* alpha, const double* target,
                      double theta_lo, double theta_hi, double* J, double* grad);
+
+/* ---- stage timing ------------------------------------------------------- */
+
+#define SPHNSE_STAGE_PREP       0  /* coefficient sets for synthesis */
+#define SPHNSE_STAGE_SYNTHESIS  1  /* per-order Legendre synthesis */
+#define SPHNSE_STAGE_RING       2  /* per-latitude FFTs and pointwise product */
+#define SPHNSE_STAGE_ANALYSIS   3  /* per-order Legendre analysis */
+#define SPHNSE_STAGE_FINISH     4  /* recombination and diagonal update */
+#define SPHNSE_STAGE_STEP       5  /* NDF vector kernels (predictor, Newton update, accept) */
+#define SPHNSE_STAGE_TRANSPOSE  6  /* order-major <-> latitude-major transposes */
+#define SPHNSE_NSTAGES          7
+
+/* enable != 0: record a CUDA event pair on the plan's stream around every
+ * later kernel launch, grouped by stage; enable == 0: stop and keep totals.
+ * Enabling clears the totals. */
+int sphnse_stage_timing(sphnse_plan* plan, int enable);
+
+/* Synchronise the plan's stream, fold the recorded events into totals and
+ * return per stage the summed device milliseconds and the number of
+ * launches (host arrays of SPHNSE_NSTAGES entries; either may be NULL). */
+int sphnse_stage_times(sphnse_plan* plan, double* ms, long* launches);
 
 /* ---- host-only helpers (no CUDA call; usable without a GPU) ------------- */
 

@@ -18,6 +18,7 @@ KEY = dict(PRECISION=1, NU=2, OMEGA=3, RTOL=4, ATOL=5, MAX_ORDER=6, NEWTON_MAX_I
            H_MAX=8, BDF=9, N_COEFF=100, L=101, NLAT=102, NLON=103, TABLE_BYTES=104)
 PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2}
 MAXK = 5
+STAGES = ("prep", "synthesis", "ring", "analysis", "finish", "step", "transpose")
 
 
 class State(ctypes.Structure):
@@ -44,6 +45,7 @@ _SIGS = {
     "sphnse_plan_destroy": (None, [ctypes.c_void_p]),
     "sphnse_plan_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "sphnse_plan_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
+    "sphnse_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "sphnse_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sphnse_grid_nodes": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p]),
     "sphnse_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -60,6 +62,8 @@ _SIGS = {
                                            ctypes.c_void_p, c_double_p]),
     "sphnse_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                         ctypes.c_double, c_double_p, ctypes.c_void_p]),
+    "sphnse_stage_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sphnse_stage_times": (ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.POINTER(ctypes.c_long)]),
     "sphnse_host_gauss_nodes": (ctypes.c_int, [ctypes.c_int, c_double_p, c_double_p, c_double_p, c_double_p]),
     "sphnse_host_legendre": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_double_p, c_double_p, c_double_p]),
 }

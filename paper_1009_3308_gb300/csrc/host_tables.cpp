@@ -134,6 +134,7 @@ bool make_fft_plan(int n, FFTPlan* p) {
     p->n = n;
     p->nstages = 0;
     int r = n;
+    while (r % 8 == 0) { p->radix[p->nstages++] = 8; r /= 8; }
     while (r % 4 == 0) { p->radix[p->nstages++] = 4; r /= 4; }
     while (r % 2 == 0) { p->radix[p->nstages++] = 2; r /= 2; }
     while (r % 3 == 0) { p->radix[p->nstages++] = 3; r /= 3; }

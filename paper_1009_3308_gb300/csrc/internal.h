@@ -85,19 +85,40 @@ struct sphnse_plan {
     double* d_tw = nullptr;      // e^{-2 pi i t / M}, M complex (FP64)
     float* d_tw32 = nullptr;     // same in FP32
     int2* d_lm = nullptr;        // (L, m) of each packed entry
+    double4_32a* d_prepc = nullptr;  // per ext row (m, K): (lam_K^{1/2}, lam_K^{-1/2}, c_down, c_up)
+    float4* d_prepc32 = nullptr; // FP32 copies of the two coefficient tables
+    float4* d_finc32 = nullptr;
+    double4_32a* d_finc = nullptr;   // per packed (L, m): (lam^{-1/2}, L eps_{L+1,m} lam^{-1/2},
+                                 //                     (L+1) eps_{L,m} lam^{-1/2}, lam)
 
     sph::Tables tab[3];
 
     // workspaces (sized for the largest field counts: 5 synthesis, 3 analysis)
     void* d_bsyn = nullptr;      // [n_ext][2 * 5] (re, im) per field, precision type
-    void* d_gsyn = nullptr;      // [5][nlat][N+1] complex
-    void* d_gana = nullptr;      // [3][nlat][N+1] complex
+    void* d_gsyn = nullptr;      // [5][N+1][nlat] complex (m-major)
+    void* d_gana = nullptr;      // [3][N+1][nlat] complex (m-major)
     void* d_hana = nullptr;      // [n_ext][2 * 3]
-    double* d_work = nullptr;    // NDF / adjoint vectors: 8 x n_coeff complex
+    void* d_gsyn_r = nullptr;    // latitude-major copies for the ring kernel: [5][nlat][N+1]
+    void* d_gana_r = nullptr;    //                                             [3][nlat][N+1]
+    double* d_work = nullptr;    // NDF / adjoint vectors (16 x n_coeff complex)
+    double* d_grid = nullptr;    // objective: two grid fields (allocated on first use)
+    double* d_theta = nullptr;
+    double* d_w = nullptr;
     double* d_tmp = nullptr;     // 2 x n_coeff complex scratch for F / J^T w
+    int n_cta = 0;               // persistent streaming grid (one CTA per SM)
+    int* d_items = nullptr;      // orders m per CTA (LPT schedule on L + 2 - m rows)
+    int* d_item_off = nullptr;   // [n_cta + 1]
+    unsigned* d_status = nullptr;  // device status word (bounded-wait timeouts)
     unsigned long long* d_norms = nullptr;  // 8 reduction slots
     double* h_norms = nullptr;   // pinned host mirror
     size_t work_bytes = 0;
+
+    // optional per-stage CUDA-event timing on the plan's stream
+    bool timing = false;
+    std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];
+    int ev_used[SPHNSE_NSTAGES] = {0};
+    double stage_ms[SPHNSE_NSTAGES] = {0};
+    long stage_n[SPHNSE_NSTAGES] = {0};
 };
 
 namespace sph {
@@ -112,12 +133,19 @@ int launch_synthesis(sphnse_plan* P, int nfields, int prec);
 int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const double* gin1,
                 double* gout0, double* gout1, double* gout2);
 int launch_analysis(sphnse_plan* P, int nfields, int prec);
+// in [nf][R][Cn] -> out [nf][Cn][R] (complex entries of the precision's type)
+int launch_transpose(sphnse_plan* P, const void* in, void* out, int R, int Cn, int nf, int prec);
 // finish: kind 0 = RHS (F = f - nu lam alpha - N), 1 = projection (N),
 // 2 = adjoint (out = -nu lam w - s_m (N_X + lam^{1/2} H_rho))
 int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha,
                   const double* forcing, double* out);
 
 int ensure_tables(sphnse_plan* P, int prec);
+bool stream_ok(const sphnse_plan* P, int prec);
+int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec);
+int launch_analysis_stream(sphnse_plan* P, int nfields, int prec);
+void stage_begin(sphnse_plan* P, int stage);
+void stage_end(sphnse_plan* P, int stage);
 int check_cuda(cudaError_t e);
 
 // whole pipelines

@@ -14,59 +14,90 @@
 
 namespace sph {
 
-__device__ __forceinline__ double eps_lm(int L, int m) {
-    if (L <= m) return 0.0;
-    double a = double(L) * L - double(m) * m;
-    return sqrt(a / (4.0 * L * L - 1.0));
-}
-
 // ---------------------------------------------------------------------------
 // prep: one thread per ext row (m, K), K = m..N+1.
 //   field 0 (zeta):  lambda_K^{1/2} alpha_K
 //   field 1 (theta): a_K = lambda_K^{-1/2} alpha_K
 //   field 2 (phi):   (K-1) eps_{K,m} a_{K-1} - (K+2) eps_{K+1,m} a_{K+1}
 // (sin(theta) d/dtheta Pt_L^m = L eps_{L+1,m} Pt_{L+1}^m - (L+1) eps_{L,m} Pt_{L-1}^m
-//  regrouped by degree).  With beta (adjoint): fields 3, 4 are the theta/phi
-// sets of beta / s_m, s_m = 1 (m = 0) or 2.
+//  regrouped by degree).  The FP64 coefficients come precomputed per row
+// (c = (lam^{1/2}, lam^{-1/2}, c_down, c_up)) so that the kernel does no
+// FP64 square roots or divisions.  With beta (adjoint): fields 3, 4 are the
+// theta/phi sets of beta / s_m, s_m = 1 (m = 0) or 2.
 template <typename T>
 __global__ void k_prep(const double2* __restrict__ alpha, const double2* __restrict__ beta,
-                       T* __restrict__ bsyn, int N, int nf) {
+                       const double4_32a* __restrict__ prepc, T* __restrict__ bsyn, int N, int nf) {
     const int m = blockIdx.y;
     const int K = m + blockIdx.x * blockDim.x + threadIdx.x;
     if (K > N + 1) return;
     const int lo = m > 0 ? m : 1;
-    auto a_of = [&](const double2* v, int Kp, double scale) -> double2 {
-        if (Kp < lo || Kp > N) return make_double2(0.0, 0.0);
-        double2 c = v[packed_index(N, m, Kp)];
-        double f = scale / sqrt(double(Kp) * (Kp + 1.0));
-        return make_double2(c.x * f, c.y * f);
+    const int row = ext_row(N, m, K);
+    const double4_32a c = prepc[row];
+    auto A = [&](const double2* v, int Kp) -> double2 {
+        return (Kp < lo || Kp > N) ? make_double2(0.0, 0.0) : v[packed_index(N, m, Kp)];
     };
-    T* out = bsyn + size_t(ext_row(N, m, K)) * (2 * nf);
-    // zeta
-    if (K >= lo && K <= N) {
-        double2 c = alpha[packed_index(N, m, K)];
-        double f = sqrt(double(K) * (K + 1.0));
-        out[0] = T(c.x * f);
-        out[1] = T(c.y * f);
-    } else {
-        out[0] = T(0);
-        out[1] = T(0);
-    }
-    const double cu = (K - 1) * eps_lm(K, m), cd = (K + 2) * eps_lm(K + 1, m);
+    T* out = bsyn + size_t(row) * (2 * nf);
     {
-        double2 aK = a_of(alpha, K, 1.0), am = a_of(alpha, K - 1, 1.0), ap = a_of(alpha, K + 1, 1.0);
-        out[2] = T(aK.x);
-        out[3] = T(aK.y);
-        out[4] = T(cu * am.x - cd * ap.x);
-        out[5] = T(cu * am.y - cd * ap.y);
+        const double2 a0 = A(alpha, K), am = A(alpha, K - 1), ap = A(alpha, K + 1);
+        out[0] = T(c.x * a0.x);
+        out[1] = T(c.x * a0.y);
+        out[2] = T(c.y * a0.x);
+        out[3] = T(c.y * a0.y);
+        out[4] = T(c.z * am.x + c.w * ap.x);
+        out[5] = T(c.z * am.y + c.w * ap.y);
     }
     if (nf == 5) {
         const double sc = m == 0 ? 1.0 : 0.5;
-        double2 aK = a_of(beta, K, sc), am = a_of(beta, K - 1, sc), ap = a_of(beta, K + 1, sc);
-        out[6] = T(aK.x);
-        out[7] = T(aK.y);
-        out[8] = T(cu * am.x - cd * ap.x);
-        out[9] = T(cu * am.y - cd * ap.y);
+        const double2 b0 = A(beta, K), bm = A(beta, K - 1), bp = A(beta, K + 1);
+        out[6] = T(sc * (c.y * b0.x));
+        out[7] = T(sc * (c.y * b0.y));
+        out[8] = T(sc * (c.z * bm.x + c.w * bp.x));
+        out[9] = T(sc * (c.z * bm.y + c.w * bp.y));
+    }
+}
+
+// FP32-path prep: alpha_K is converted once per row and its degree
+// neighbours come from shared memory; the arithmetic is FP32 (the FP32 path
+// contracts in FP32 anyway), keeping the weak FP64 pipe for the state only.
+__global__ void __launch_bounds__(128) k_prep32(const double2* __restrict__ alpha, const double2* __restrict__ beta,
+                                                const float4* __restrict__ prepc, float* __restrict__ bsyn, int N,
+                                                int nf) {
+    __shared__ float2 sa[130], sb[130];
+    const int m = blockIdx.y, t = threadIdx.x;
+    const int K0 = m + blockIdx.x * 128, K = K0 + t;
+    const int lo = m > 0 ? m : 1;
+    const float sc = m == 0 ? 1.f : 0.5f;
+    auto ld = [&](const double2* v, int Kp, float scale) -> float2 {
+        if (Kp < lo || Kp > N) return make_float2(0.f, 0.f);
+        const double2 c = v[packed_index(N, m, Kp)];
+        return make_float2(float(c.x) * scale, float(c.y) * scale);
+    };
+    sa[t + 1] = ld(alpha, K, 1.f);
+    if (t == 0) sa[0] = ld(alpha, K0 - 1, 1.f);
+    if (t == 127) sa[129] = ld(alpha, K0 + 128, 1.f);
+    if (nf == 5) {
+        sb[t + 1] = ld(beta, K, sc);
+        if (t == 0) sb[0] = ld(beta, K0 - 1, sc);
+        if (t == 127) sb[129] = ld(beta, K0 + 128, sc);
+    }
+    __syncthreads();
+    if (K > N + 1) return;
+    const int row = ext_row(N, m, K);
+    const float4 c = prepc[row];
+    float* out = bsyn + size_t(row) * (2 * nf);
+    const float2 a0 = sa[t + 1], am = sa[t], ap = sa[t + 2];
+    out[0] = c.x * a0.x;
+    out[1] = c.x * a0.y;
+    out[2] = c.y * a0.x;
+    out[3] = c.y * a0.y;
+    out[4] = fmaf(c.z, am.x, c.w * ap.x);
+    out[5] = fmaf(c.z, am.y, c.w * ap.y);
+    if (nf == 5) {
+        const float2 b0 = sb[t + 1], bm = sb[t], bp = sb[t + 2];
+        out[6] = c.y * b0.x;
+        out[7] = c.y * b0.y;
+        out[8] = fmaf(c.z, bm.x, c.w * bp.x);
+        out[9] = fmaf(c.z, bm.y, c.w * bp.y);
     }
 }
 
@@ -129,7 +160,7 @@ __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, c
                 outr = -gr * inv_s;
                 outi = -gi * inv_s;
             }
-            T* dst = gsyn + ((size_t(f) * nlat + row) * ld + m) * 2;
+            T* dst = gsyn + ((size_t(f) * ld + m) * nlat + row) * 2;
             dst[0] = outr;
             dst[1] = outi;
         }
@@ -156,10 +187,10 @@ __global__ void __launch_bounds__(128) k_analysis(const T* __restrict__ pana, co
     for (int i = threadIdx.x; i < nh * NF; i += blockDim.x) {
         const int p = i / NF, f = i % NF;
         const int pr = nlat - 1 - p;
-        const T* a = gana + ((size_t(f) * nlat + p) * ld + m) * 2;
+        const T* a = gana + ((size_t(f) * ld + m) * nlat + p) * 2;
         T ar = a[0], ai = a[1], br = T(0), bi = T(0);
         if (pr != p) {
-            const T* b = gana + ((size_t(f) * nlat + pr) * ld + m) * 2;
+            const T* b = gana + ((size_t(f) * ld + m) * nlat + pr) * 2;
             br = b[0];
             bi = b[1];
         }
@@ -189,18 +220,20 @@ __global__ void __launch_bounds__(128) k_analysis(const T* __restrict__ pana, co
 // finish: one thread per packed (L, m).
 //   N_{L,m} = lambda^{-1/2} [ -i m H^theta_L
 //             - (L eps_{L+1,m} H^phi_{L+1} - (L+1) eps_{L,m} H^phi_{L-1}) ]
+// with the FP64 coefficients precomputed per entry:
+// c = (lambda^{-1/2}, L eps_{L+1,m} lambda^{-1/2}, (L+1) eps_{L,m} lambda^{-1/2}, lambda).
 // kind 0: out = forcing - nu lambda alpha - N              (Eq. (ode))
 // kind 1: out = N                                          (projection)
 // kind 2: out = -nu lambda w - s_m (N + lambda^{1/2} H^rho_L)  (J^T w; alpha = w)
 template <typename T>
 __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const double2* __restrict__ alpha,
                          const double2* __restrict__ forcing, double2* __restrict__ out,
-                         const int2* __restrict__ lm, int N, double nu, int n) {
+                         const int2* __restrict__ lm, const double4_32a* __restrict__ finc, int N, double nu,
+                         int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int L = lm[i].x, m = lm[i].y;
-    const double lam = double(L) * (L + 1.0);
-    const double isl = 1.0 / sqrt(lam);
+    const double4_32a c = finc[i];
     const T* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
     const T* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
     const double htr = double(hL[0]), hti = double(hL[1]);
@@ -211,13 +244,14 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
         hdr = double(hD[2]);
         hdi = double(hD[3]);
     }
-    const double eu = L * eps_lm(L + 1, m), ed = (L + 1) * eps_lm(L, m);
-    const double nr = isl * (m * hti - (eu * hur - ed * hdr));
-    const double ni = isl * (-m * htr - (eu * hui - ed * hdi));
+    const double cm = c.x * m;
+    const double nr = cm * hti - (c.y * hur - c.z * hdr);
+    const double ni = -cm * htr - (c.y * hui - c.z * hdi);
+    const double lam = c.w;
     double2 r;
     if (kind == 0) {
         const double2 a = alpha[i];
-        double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
+        const double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
         r.x = f.x - nu * lam * a.x - nr;
         r.y = f.y - nu * lam * a.y - ni;
     } else if (kind == 1) {
@@ -225,9 +259,51 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
     } else {
         const double2 wv = alpha[i];
         const double sm = m == 0 ? 1.0 : 2.0;
-        const double sl = sqrt(lam);
+        const double sl = lam * c.x;  // lambda^{1/2}
         r.x = -nu * lam * wv.x - sm * (nr + sl * double(hL[4]));
         r.y = -nu * lam * wv.y - sm * (ni + sl * double(hL[5]));
+    }
+    out[i] = r;
+}
+
+// FP32-path finish: the recombination runs in FP32 on the FP32 projections
+// (coefficients in FP32); only the state update f - nu lambda alpha - N is
+// FP64.
+__global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, const double2* __restrict__ alpha,
+                           const double2* __restrict__ forcing, double2* __restrict__ out,
+                           const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = lm[i].x, m = lm[i].y;
+    const float4 c = finc[i];
+    const float* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
+    const float* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
+    float hdr = 0.f, hdi = 0.f;
+    if (L - 1 >= m) {
+        const float* hD = hana + size_t(ext_row(N, m, L - 1)) * 2 * nf;
+        hdr = hD[2];
+        hdi = hD[3];
+    }
+    const float cm = c.x * float(m);
+    const float nr = cm * hL[1] - (c.y * hU[2] - c.z * hdr);
+    const float ni = -cm * hL[0] - (c.y * hU[3] - c.z * hdi);
+    const double lam = double(L) * double(L + 1);
+    double2 r;
+    if (kind == 0) {
+        const double2 a = alpha[i];
+        const double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
+        const double nl = nu * lam;
+        r.x = fma(-nl, a.x, f.x) - double(nr);
+        r.y = fma(-nl, a.y, f.y) - double(ni);
+    } else if (kind == 1) {
+        r = make_double2(double(nr), double(ni));
+    } else {
+        const double2 wv = alpha[i];
+        const float sm = m == 0 ? 1.f : 2.f;
+        const float sl = c.w * c.x;  // lambda^{1/2}
+        const double nl = nu * lam;
+        r.x = -nl * wv.x - double(sm * (nr + sl * hL[4]));
+        r.y = -nl * wv.y - double(sm * (ni + sl * hL[5]));
     }
     out[i] = r;
 }
@@ -239,27 +315,45 @@ template <typename T>
 static int prep_t(sphnse_plan* P, const double* alpha, const double* beta) {
     const int nf = beta ? 5 : 3;
     dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1);
+    stage_begin(P, SPHNSE_STAGE_PREP);
     k_prep<T><<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
-                                           reinterpret_cast<const double2*>(beta),
+                                           reinterpret_cast<const double2*>(beta), P->d_prepc,
                                            reinterpret_cast<T*>(P->d_bsyn), P->N, nf);
+    stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
 
 int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int prec) {
-    return prec == SPHNSE_FP64 ? prep_t<double>(P, alpha, beta) : prep_t<float>(P, alpha, beta);
+    if (prec == SPHNSE_FP64) return prep_t<double>(P, alpha, beta);
+    const int nf = beta ? 5 : 3;
+    dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1);
+    stage_begin(P, SPHNSE_STAGE_PREP);
+    k_prep32<<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
+                                         reinterpret_cast<const double2*>(beta), P->d_prepc32,
+                                         reinterpret_cast<float*>(P->d_bsyn), P->N, nf);
+    stage_end(P, SPHNSE_STAGE_PREP);
+    return check_cuda(cudaGetLastError());
 }
 
 template <typename T, int NF>
 static int synth_t(sphnse_plan* P) {
     dim3 blk(128), grd((P->nh + 127) / 128, P->N + 1);
     size_t sm = size_t(P->N + 2) * 2 * NF * sizeof(T);
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_synthesis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     k_synthesis<T, NF><<<grd, blk, sm, P->stream>>>(
         reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
         reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn), P->d_s, P->N, P->nh, P->nlat);
+    stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(cudaGetLastError());
 }
 
 int launch_synthesis(sphnse_plan* P, int nfields, int prec) {
+    if (stream_ok(P, prec)) {
+        int rc = launch_synthesis_stream(P, nfields, prec);
+        if (rc != SPHNSE_E_UNSUPPORTED) return rc;
+    }
     if (prec == SPHNSE_FP64) return nfields == 5 ? synth_t<double, 5>(P) : synth_t<double, 3>(P);
     return nfields == 5 ? synth_t<float, 5>(P) : synth_t<float, 3>(P);
 }
@@ -272,13 +366,19 @@ static int anal_t(sphnse_plan* P) {
     if (sm > 48 * 1024) {
         cudaFuncSetAttribute(k_analysis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     }
+    stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     k_analysis<T, NF><<<grd, blk, sm, P->stream>>>(
         reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].ana),
         reinterpret_cast<const T*>(P->d_gana), reinterpret_cast<T*>(P->d_hana), P->N, P->nh, P->nlat);
+    stage_end(P, SPHNSE_STAGE_ANALYSIS);
     return check_cuda(cudaGetLastError());
 }
 
 int launch_analysis(sphnse_plan* P, int nfields, int prec) {
+    if (stream_ok(P, prec)) {
+        int rc = launch_analysis_stream(P, nfields, prec);
+        if (rc != SPHNSE_E_UNSUPPORTED) return rc;
+    }
     if (prec == SPHNSE_FP64) return nfields == 3 ? anal_t<double, 3>(P) : anal_t<double, 2>(P);
     return nfields == 3 ? anal_t<float, 3>(P) : anal_t<float, 2>(P);
 }
@@ -288,16 +388,18 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
     const int n = P->n_coeff;
     const int nf = kind == 2 ? 3 : 2;
     dim3 blk(256), grd((n + 255) / 256);
+    stage_begin(P, SPHNSE_STAGE_FINISH);
     if (prec == SPHNSE_FP64)
         k_finish<double><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const double*>(P->d_hana), nf,
                                                      reinterpret_cast<const double2*>(alpha),
                                                      reinterpret_cast<const double2*>(forcing),
-                                                     reinterpret_cast<double2*>(out), P->d_lm, P->N, P->nu, n);
+                                                     reinterpret_cast<double2*>(out), P->d_lm, P->d_finc, P->N, P->nu, n);
     else
-        k_finish<float><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const float*>(P->d_hana), nf,
-                                                    reinterpret_cast<const double2*>(alpha),
-                                                    reinterpret_cast<const double2*>(forcing),
-                                                    reinterpret_cast<double2*>(out), P->d_lm, P->N, P->nu, n);
+        k_finish32<<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const float*>(P->d_hana), nf,
+                                               reinterpret_cast<const double2*>(alpha),
+                                               reinterpret_cast<const double2*>(forcing),
+                                               reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n);
+    stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }
 

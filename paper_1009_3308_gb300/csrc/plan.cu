@@ -15,6 +15,40 @@ namespace sph {
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? SPHNSE_OK : SPHNSE_E_CUDA; }
 
+static void fold_stage_events(sphnse_plan* P) {
+    cudaStreamSynchronize(P->stream);
+    for (int s = 0; s < SPHNSE_NSTAGES; ++s) {
+        for (int i = 0; i + 1 < P->ev_used[s]; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, P->ev[s][i], P->ev[s][i + 1]) == cudaSuccess) {
+                P->stage_ms[s] += ms;
+                P->stage_n[s] += 1;
+            }
+        }
+        P->ev_used[s] = 0;
+    }
+}
+
+static void record_stage_event(sphnse_plan* P, int stage) {
+    auto& v = P->ev[stage];
+    if (P->ev_used[stage] >= int(v.size())) {
+        if (v.size() >= 1 << 16) fold_stage_events(P);  // bound the pool
+        if (P->ev_used[stage] >= int(v.size())) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            v.push_back(e);
+        }
+    }
+    cudaEventRecord(v[P->ev_used[stage]++], P->stream);
+}
+
+void stage_begin(sphnse_plan* P, int stage) {
+    if (P->timing) record_stage_event(P, stage);
+}
+void stage_end(sphnse_plan* P, int stage) {
+    if (P->timing) record_stage_event(P, stage);
+}
+
 static void free_tables(Tables& t) {
     if (t.syn) cudaFree(t.syn);
     if (t.ana) cudaFree(t.ana);
@@ -90,7 +124,9 @@ int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, doubl
         return SPHNSE_E_UNSUPPORTED;
     }
     if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
     if ((rc = launch_ring(P, RING_RHS, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
+    if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
     if ((rc = launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 0, prec, alpha, forcing, out);
 }
@@ -103,7 +139,9 @@ int rhs_adjoint_device(sphnse_plan* P, const double* alpha, const double* w, dou
     int rc;
     if ((rc = launch_prep(P, alpha, w, prec))) return rc;
     if ((rc = launch_synthesis(P, 5, prec))) return rc;
+    if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 5, prec))) return rc;
     if ((rc = launch_ring(P, RING_ADJOINT, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
+    if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 3, prec))) return rc;
     if ((rc = launch_analysis(P, 3, prec))) return rc;
     return launch_finish(P, 2, prec, w, nullptr, out);
 }
@@ -119,11 +157,14 @@ static void destroy_plan(sphnse_plan* P) {
     if (P->stream) cudaStreamSynchronize(P->stream);
     else cudaDeviceSynchronize();
     for (auto& t : P->tab) free_tables(t);
-    void* ptrs[] = {P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_lm, P->d_bsyn,
-                    P->d_gsyn, P->d_gana, P->d_hana, P->d_work, P->d_tmp, P->d_norms};
+    void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
+                    P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
+                    P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (P->h_norms) cudaFreeHost(P->h_norms);
+    for (auto& v : P->ev)
+        for (auto e : v) cudaEventDestroy(e);
     delete P;
 }
 
@@ -163,7 +204,8 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
         return nullptr;
     }
     FFTPlan fft;
-    if (!make_fft_plan(nlon, &fft)) {
+    // the ring kernel keeps at most 3 butterflies per thread with <= 256 threads
+    if (!make_fft_plan(nlon, &fft) || nlon > 1536) {
         g_last_error = SPHNSE_E_UNSUPPORTED;
         return nullptr;
     }
@@ -206,8 +248,29 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
         tw32[2 * t + 1] = float(tw[2 * t + 1]);
     }
     std::vector<int2> lm(P->n_coeff);
+    std::vector<double4_32a> finc(P->n_coeff), prepc(P->n_ext);
+    auto eps = [](int l, int m) {
+        return l <= m ? 0.0 : std::sqrt((double(l) * l - double(m) * m) / (4.0 * l * l - 1.0));
+    };
     for (int m = 0, i = 0; m <= L; ++m)
-        for (int l = (m > 0 ? m : 1); l <= L; ++l) lm[i++] = make_int2(l, m);
+        for (int l = (m > 0 ? m : 1); l <= L; ++l) {
+            lm[i] = make_int2(l, m);
+            const double lam = double(l) * (l + 1.0), isl = 1.0 / std::sqrt(lam);
+            finc[i] = make_double4_32a(isl, l * eps(l + 1, m) * isl, (l + 1) * eps(l, m) * isl, lam);
+            ++i;
+        }
+    // prep: zeta set lam^{1/2} a_K, theta set lam^{-1/2} a_K, phi set
+    // (K-1) eps_{K,m} lam_{K-1}^{-1/2} a_{K-1} - (K+2) eps_{K+1,m} lam_{K+1}^{-1/2} a_{K+1}
+    for (int m = 0; m <= L; ++m) {
+        const int lo = m > 0 ? m : 1;
+        auto isl = [&](int k) { return (k < lo || k > L) ? 0.0 : 1.0 / std::sqrt(double(k) * (k + 1.0)); };
+        for (int K = m; K <= L + 1; ++K) {
+            const bool in = K >= lo && K <= L;
+            prepc[ext_row(L, m, K)] = make_double4_32a(in ? std::sqrt(double(K) * (K + 1.0)) : 0.0, isl(K),
+                                                   (K - 1) * eps(K, m) * isl(K - 1),
+                                                   -(K + 2) * eps(K + 1, m) * isl(K + 1));
+        }
+    }
     const size_t nc = size_t(P->n_coeff);
     const size_t sz_g = size_t(nlat) * (L + 1) * 2 * sizeof(double);
     if (!rc) rc = dalloc(&P->d_x, nlat * sizeof(double));
@@ -216,10 +279,16 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     if (!rc) rc = dalloc(&P->d_tw, tw.size() * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tw32, tw32.size() * sizeof(float));
     if (!rc) rc = dalloc(&P->d_lm, nc * sizeof(int2));
+    if (!rc) rc = dalloc(&P->d_finc, nc * sizeof(double4_32a));
+    if (!rc) rc = dalloc(&P->d_prepc, size_t(P->n_ext) * sizeof(double4_32a));
+    if (!rc) rc = dalloc(&P->d_finc32, nc * sizeof(float4));
+    if (!rc) rc = dalloc(&P->d_prepc32, size_t(P->n_ext) * sizeof(float4));
     if (!rc) rc = dalloc(&P->d_bsyn, size_t(P->n_ext) * 10 * sizeof(double));
     if (!rc) rc = dalloc(&P->d_gsyn, 5 * sz_g);
     if (!rc) rc = dalloc(&P->d_gana, 3 * sz_g);
     if (!rc) rc = dalloc(&P->d_hana, size_t(P->n_ext) * 6 * sizeof(double));
+    if (!rc) rc = dalloc(&P->d_gsyn_r, 5 * sz_g);
+    if (!rc) rc = dalloc(&P->d_gana_r, 3 * sz_g);
     if (!rc) rc = dalloc(&P->d_work, 16 * nc * 2 * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tmp, 2 * nc * 2 * sizeof(double));
     if (!rc) rc = dalloc(&P->d_norms, 16 * sizeof(unsigned long long));
@@ -234,6 +303,46 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     up(P->d_tw, tw.data(), tw.size() * sizeof(double));
     up(P->d_tw32, tw32.data(), tw32.size() * sizeof(float));
     up(P->d_lm, lm.data(), nc * sizeof(int2));
+    up(P->d_finc, finc.data(), nc * sizeof(double4_32a));
+    up(P->d_prepc, prepc.data(), size_t(P->n_ext) * sizeof(double4_32a));
+    {
+        std::vector<float4> f32(nc), p32(P->n_ext);
+        for (size_t i = 0; i < nc; ++i)
+            f32[i] = make_float4(float(finc[i].x), float(finc[i].y), float(finc[i].z), float(finc[i].w));
+        for (size_t i = 0; i < size_t(P->n_ext); ++i)
+            p32[i] = make_float4(float(prepc[i].x), float(prepc[i].y), float(prepc[i].z), float(prepc[i].w));
+        up(P->d_finc32, f32.data(), nc * sizeof(float4));
+        up(P->d_prepc32, p32.data(), size_t(P->n_ext) * sizeof(float4));
+    }
+    // LPT schedule of the orders m (cost L + 2 - m table rows) over one
+    // persistent CTA per SM for the streaming Legendre kernels
+    if (!rc) {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
+        if (nsm < 1) nsm = 1;
+        const int G = nsm < L + 1 ? nsm : L + 1;
+        std::vector<std::vector<int>> bins(G);
+        std::vector<long> load(G, 0);
+        for (int m = 0; m <= L; ++m) {  // costs decrease with m
+            int b = 0;
+            for (int k = 1; k < G; ++k)
+                if (load[k] < load[b]) b = k;
+            bins[b].push_back(m);
+            load[b] += L + 2 - m;
+        }
+        std::vector<int> items, off(1, 0);
+        for (auto& bi : bins) {
+            items.insert(items.end(), bi.begin(), bi.end());
+            off.push_back(int(items.size()));
+        }
+        P->n_cta = G;
+        rc = dalloc(&P->d_items, items.size() * sizeof(int));
+        if (!rc) rc = dalloc(&P->d_item_off, off.size() * sizeof(int));
+        if (!rc) rc = dalloc(&P->d_status, sizeof(unsigned));
+        up(P->d_items, items.data(), items.size() * sizeof(int));
+        up(P->d_item_off, off.data(), off.size() * sizeof(int));
+        if (!rc && cudaMemset(P->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = SPHNSE_E_CUDA;
+    }
     if (!rc) rc = ensure_tables(P, SPHNSE_FP64);
     if (rc) {
         destroy_plan(P);
@@ -324,6 +433,7 @@ int sphnse_grid_fields(sphnse_plan* P, const double* alpha, double* zeta, double
     int rc;
     if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
     if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
     return launch_ring(P, RING_GRID, prec, nullptr, nullptr, zeta, uth, uph);
 }
 
@@ -332,8 +442,44 @@ int sphnse_project(sphnse_plan* P, const double* vth, const double* vph, double*
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
     int rc;
     if ((rc = launch_ring(P, RING_PROJECT, prec, vth, vph, nullptr, nullptr, nullptr))) return rc;
+    if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
     if ((rc = launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 1, prec, nullptr, nullptr, out);
+}
+
+int sphnse_sync(sphnse_plan* P) {
+    if (!P) return SPHNSE_E_ARG;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return SPHNSE_E_CUDA;
+    unsigned st = 0;
+    if (cudaMemcpy(&st, P->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SPHNSE_E_CUDA;
+    if (st) {
+        cudaMemset(P->d_status, 0, sizeof(unsigned));
+        return SPHNSE_E_TIMEOUT;
+    }
+    return SPHNSE_OK;
+}
+
+int sphnse_stage_timing(sphnse_plan* P, int enable) {
+    if (!P) return SPHNSE_E_ARG;
+    if (enable) {
+        fold_stage_events(P);
+        for (int s = 0; s < SPHNSE_NSTAGES; ++s) {
+            P->stage_ms[s] = 0;
+            P->stage_n[s] = 0;
+        }
+    }
+    P->timing = enable != 0;
+    return SPHNSE_OK;
+}
+
+int sphnse_stage_times(sphnse_plan* P, double* ms, long* launches) {
+    if (!P) return SPHNSE_E_ARG;
+    fold_stage_events(P);
+    for (int s = 0; s < SPHNSE_NSTAGES; ++s) {
+        if (ms) ms[s] = P->stage_ms[s];
+        if (launches) launches[s] = P->stage_n[s];
+    }
+    return SPHNSE_OK;
 }
 
 // host-only helpers (no CUDA): the FP64 precompute, exposed for checks
