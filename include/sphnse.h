@@ -51,6 +51,7 @@ extern "C" {
 #define SPHNSE_E_STEP_TOO_SMALL   -6  /* the adaptive step fell below 16 eps |t| */
 #define SPHNSE_E_TIMEOUT          -7  /* a bounded device wait ran out */
 #define SPHNSE_E_UNSUPPORTED      -8  /* nlon not 2^a 3^b or above 1536, or a precision not built */
+#define SPHNSE_E_TOO_LARGE        -9  /* size beyond the fixed scratch of an allocation-free entry point */
 
 /* ---- plan parameters (sphnse_plan_set / sphnse_plan_get) ---------------- */
 #define SPHNSE_KEY_PRECISION       1  /* SPHNSE_FP64 | SPHNSE_FP32 | SPHNSE_BF16X3 (default FP64) */
@@ -244,6 +245,31 @@ int sphnse_stage_timing(sphnse_plan* plan, int enable);
  * return per stage the summed device milliseconds and the number of
  * launches (host arrays of SPHNSE_NSTAGES entries; either may be NULL). */
 int sphnse_stage_times(sphnse_plan* plan, double* ms, long* launches);
+
+/* ---- allocation-free entry point ---------------------------------------- */
+
+/* The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- a caller whose device memory is entirely owned by a
+ * framework's caching allocator (where a raw cudaMalloc can fail or
+ * fragment the pool), or a latency-critical loop that cannot afford the
+ * device synchronisation and the milliseconds of an allocation -- and that
+ * may hold no plan, since creating one allocates.
+ *
+ * Writes *out = <w, dF/dnu> = -sum_{packed (L,m)} L(L+1) (Re alpha Re w +
+ * Im alpha Im w), the value sphnse_rhs_adjoint adds to its nu_bar, for
+ * packed complex128 vectors alpha, w of truncation L (n = (L+1)(L+2)/2 - 1
+ * entries).  alpha, w, out: device pointers owned by the caller (out: one
+ * double); stream: cudaStream_t or NULL.  Stream-ordered, no host sync.
+ * Allocates nothing: block partial sums go to a file-scope device array of
+ * SPHNSE_NOALLOC_MAX_BLOCKS doubles (32 KB per device that loads the
+ * library, held until the process exits).  Sizes with n > 2048 *
+ * SPHNSE_NOALLOC_MAX_BLOCKS (L above about 4090) return SPHNSE_E_TOO_LARGE.
+ * The first call on a device looks up the array's device address with that
+ * device current (a one-time set-up); make that first call before any
+ * stream capture.  All calls share the array and each call overwrites the
+ * slots it reads; calls that overlap on the GPU race on it. */
+#define SPHNSE_NOALLOC_MAX_BLOCKS 4096
+int sphnse_nu_sensitivity_noalloc(int L, const double* alpha, const double* w, double* out, void* stream);
 
 /* ---- host-only helpers (no CUDA call; usable without a GPU) ------------- */
 

@@ -188,6 +188,7 @@ const char* sphnse_error_string(int code) {
         case SPHNSE_E_STEP_TOO_SMALL: return "step size below minimum";
         case SPHNSE_E_TIMEOUT: return "bounded device wait timed out";
         case SPHNSE_E_UNSUPPORTED: return "unsupported configuration";
+        case SPHNSE_E_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free entry point";
         default: return "unknown status";
     }
 }
