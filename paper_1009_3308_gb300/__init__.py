@@ -73,6 +73,10 @@ class Plan:
         self.set("PRECISION", PRECISION[precision])
         self.precision = precision
 
+    def sync(self):
+        """Wait for the plan's stream; raises on a device-side timeout."""
+        return check("sphnse_sync", _capi.lib().sphnse_sync(self._h))
+
     @property
     def handle(self):
         return self._h

@@ -62,6 +62,22 @@ struct Tables {
     bool built = false;
 };
 
+// tcgen05 path state (tensor maps and item schedules, built on first use)
+struct TcState {
+    void* map_hi = nullptr;      // CUtensorMap per (m, parity) block, global memory
+    void* map_lo = nullptr;
+    int4* ana_items = nullptr;
+    int* ana_off = nullptr;
+    int ana_cta = 0;
+    bool ana_ready = false;
+    void* smap_hi = nullptr;     // synthesis: tensor maps of the transposed tables
+    void* smap_lo = nullptr;
+    void* tsyn_hi = nullptr;     // transposed padded bf16 tables [block][nh][pad8(n)]
+    void* tsyn_lo = nullptr;
+    size_t tsyn_bytes = 0;
+    bool syn_ready = false;
+};
+
 }  // namespace sph
 
 struct sphnse_plan {
@@ -92,6 +108,7 @@ struct sphnse_plan {
                                  //                     (L+1) eps_{L,m} lam^{-1/2}, lam)
 
     sph::Tables tab[3];
+    sph::TcState tc;
 
     // workspaces (sized for the largest field counts: 5 synthesis, 3 analysis)
     void* d_bsyn = nullptr;      // [n_ext][2 * 5] (re, im) per field, precision type
@@ -143,6 +160,10 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha,
 int ensure_tables(sphnse_plan* P, int prec);
 bool stream_ok(const sphnse_plan* P, int prec);
 int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec);
+bool tc_supported(const sphnse_plan* P);
+int launch_analysis_tc(sphnse_plan* P, int nfields);
+int launch_synthesis_tc(sphnse_plan* P);
+void tc_free(sphnse_plan* P);
 int launch_analysis_stream(sphnse_plan* P, int nfields, int prec);
 void stage_begin(sphnse_plan* P, int stage);
 void stage_end(sphnse_plan* P, int stage);

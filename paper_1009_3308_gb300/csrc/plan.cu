@@ -119,15 +119,13 @@ int ensure_tables(sphnse_plan* P, int prec) {
 int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, double* out) {
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
     int rc;
+    const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
     if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
-    if (P->precision == SPHNSE_BF16X3) {
-        return SPHNSE_E_UNSUPPORTED;
-    }
-    if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    if ((rc = tc ? launch_synthesis_tc(P) : launch_synthesis(P, 3, prec))) return rc;
     if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
     if ((rc = launch_ring(P, RING_RHS, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
     if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
-    if ((rc = launch_analysis(P, 2, prec))) return rc;
+    if ((rc = tc ? launch_analysis_tc(P, 2) : launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 0, prec, alpha, forcing, out);
 }
 
@@ -157,6 +155,7 @@ static void destroy_plan(sphnse_plan* P) {
     if (P->stream) cudaStreamSynchronize(P->stream);
     else cudaDeviceSynchronize();
     for (auto& t : P->tab) free_tables(t);
+    tc_free(P);
     void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
                     P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
                     P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};
@@ -402,7 +401,7 @@ int sphnse_plan_get(const sphnse_plan* P, int key, double* v) {
         case SPHNSE_KEY_NLAT: *v = P->nlat; break;
         case SPHNSE_KEY_NLON: *v = P->nlon; break;
         case SPHNSE_KEY_TABLE_BYTES: {
-            double b = 0;
+            double b = double(P->tc.tsyn_bytes);
             for (const auto& t : P->tab) b += double(t.bytes);
             *v = b;
             break;

@@ -1,0 +1,100 @@
+// tcgen05 (5th-generation tensor core) helpers for sm_103a, inline PTX:
+// tensor-memory allocation, BF16 MMA with FP32 accumulation in TMEM,
+// commit-to-mbarrier, TMEM -> register loads, 2-D TMA tile loads and the
+// shared-memory matrix descriptors of the 128-byte-swizzled K-major layout.
+#pragma once
+#include <cstdint>
+
+#include "ptx.cuh"
+
+namespace sph {
+
+// ---- tensor memory ----------------------------------------------------------
+// executed by one full warp; writes the TMEM base address to *dst (smem)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ---- MMA ------------------------------------------------------------------
+// D(tmem) (+)= A(smem desc) x B(smem desc), kind::f16 (BF16 in, FP32 accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on the mbarrier once every previously issued MMA of this thread completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// instruction descriptor: D = F32, A = B = BF16, both K-major, shape M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// shared-memory descriptor, K-major, 128-byte swizzle: rows of 128 bytes,
+// 8-row (1024-byte) swizzle atoms stacked every 1024 bytes along M/N.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* smem_ptr) {
+    const uint32_t a = smem_u32(smem_ptr);
+    uint64_t d = 0;
+    d |= uint64_t((a & 0x3FFFF) >> 4);            // start address
+    d |= uint64_t(1) << 16;                       // leading byte offset (unused with swizzle)
+    d |= uint64_t(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+    d |= uint64_t(1) << 46;                       // descriptor version
+    d |= uint64_t(2) << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// byte offset of element (row, k) of a K-major 128B-swizzled tile whose rows
+// hold 64 bf16 (128 bytes): 16-byte chunk index XOR (row mod 8)
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+    return uint32_t(row) * 128u + ((uint32_t(k >> 3) ^ uint32_t(row & 7)) << 4) + uint32_t(k & 7) * 2u;
+}
+
+// ---- TMEM -> registers ------------------------------------------------------
+// 32 lanes x 16 columns of 32-bit: thread l of the warp gets row (lane base + l)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- TMA ----------------------------------------------------------------------
+// 2-D tiled load (coordinates in elements; x innermost, multiple of 8 for bf16)
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar,
+                                            uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+}  // namespace sph

@@ -1,0 +1,55 @@
+"""BF16 hi + lo split-precision Legendre contractions on tcgen05 tensor
+cores (FP32 accumulation), checked against the FP64 oracle.
+
+Error budget: each operand is split as x = hi + lo with hi, lo in BF16
+(8-bit significands), so |x - hi - lo| <= 2^-17 |x|; the product keeps
+hi*hi + hi*lo + lo*hi and drops lo*lo (<= 2^-16 relative); FP32
+accumulation adds ~2^-24 sqrt(n).  Per contraction output the relative
+error is ~1e-5 of the sum of |terms|; the tests take 1e-4 on F (norm) and
+state the measured error."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.rhs import Problem, rhs_separable
+from seeded_inputs import coefficients, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("L,nlon,nu,Om,decay", [(127, 384, 1e-4, 1.0, 0.05), (255, 768, 1e-4, 1.0, 0.05)])
+def test_rhs_bf16x3_matches_oracle(L, nlon, nu, Om, decay):
+    from paper_1009_3308_gb300 import Plan
+    prob = Problem(L, nlon, nu, Om)
+    a = coefficients(L, 400 + L, decay) * 3.0
+    ref = rhs_separable(prob, a)
+    plan = Plan(L, nlon // 2, nlon, nu, Om, precision="bf16x3")
+    got = plan.rhs(_dev(a)).cpu().numpy()
+    err = _rel(got, ref)
+    print(f"L={L} bf16x3 rel err {err:.3e}")
+    assert err <= 1e-4, err
+    assert plan.sync() == 0
+
+
+def test_rhs_bf16x3_L511_vs_fp64():
+    from paper_1009_3308_gb300 import Plan
+    w = workload("L511")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"])
+    a = _dev(w["alpha0"])
+    f64 = plan.rhs(a).cpu().numpy()
+    plan.set_precision("bf16x3")
+    fb = plan.rhs(a).cpu().numpy()
+    err = _rel(fb, f64)
+    print(f"L=511 bf16x3 vs fp64 rel err {err:.3e}")
+    assert err <= 1e-4, err
+    assert plan.sync() == 0
