@@ -225,6 +225,42 @@ int sphnse_adjoint_init(sphnse_plan* plan, double h0, const double* alpha0,
 int sphnse_objective(sphnse_plan* plan, const double* alpha, const double* target,
                      double theta_lo, double theta_hi, double* J, double* grad);
 
+/* ---- batched ensemble ----------------------------------------------------- */
+
+typedef struct sphnse_ensemble sphnse_ensemble;
+
+/* n independent problems with truncations L[i] and viscosities nu[i] (host
+ * arrays), common Omega, each on its Gauss-rectangle grid with nlon the
+ * smallest even 2^a 3^b >= 3 L + 2 (nlat = nlon / 2).  Instances of equal L
+ * share one set of Legendre tables and run every RHS stage as one launch over
+ * all of them; FP32 contractions, FP64 state.  Supported L: those whose
+ * northern node count nlat/2 is a multiple of 4 and >= 32 (e.g. 63, 127, 255).
+ * The ensemble owns its state vectors (see sphnse_ensemble_instance).
+ * Returns NULL on error. */
+sphnse_ensemble* sphnse_ensemble_create(int n, const int* L, const double* nu, double Omega);
+void sphnse_ensemble_destroy(sphnse_ensemble* ens);
+
+/* SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX (and
+ * _PRECISION, FP32 only). */
+int sphnse_ensemble_set(sphnse_ensemble* ens, int key, double value);
+int sphnse_ensemble_set_stream(sphnse_ensemble* ens, void* stream);
+
+/* Device pointers (owned by the ensemble) of instance i's packed state alpha
+ * and of its last RHS F (complex128, n_coeff entries); any output may be NULL. */
+int sphnse_ensemble_instance(sphnse_ensemble* ens, int i, double** alpha, double** F, int* n_coeff);
+
+/* F_i = F(alpha_i) for every instance (Eq. (ode)), as one CUDA-graph launch. */
+int sphnse_ensemble_rhs(sphnse_ensemble* ens);
+
+/* Initialise every instance's NDF state at t0 from its current alpha
+ * (automatic initial step per instance, as sphnse_state_init). */
+int sphnse_ensemble_init(sphnse_ensemble* ens, double t0);
+
+/* One accepted step of every instance, each with its own adaptive step size
+ * and order (the controller of sphnse_step), advanced in lockstep by attempt
+ * and Newton iteration; info: host array of n entries or NULL. */
+int sphnse_ensemble_step(sphnse_ensemble* ens, sphnse_step_info* info);
+
 /* ---- stage timing ------------------------------------------------------- */
 
 #define SPHNSE_STAGE_PREP       0  /* coefficient sets for synthesis */

@@ -14,7 +14,7 @@ import math
 from . import _capi
 from ._capi import KEY, MAXK, PRECISION, SphnseError, State, StepInfo, check
 
-__all__ = ["Plan", "SphnseError", "PRECISION", "MAXK", "n_coeff"]
+__all__ = ["Plan", "Integrator", "Ensemble", "SphnseError", "PRECISION", "MAXK", "n_coeff"]
 
 
 def n_coeff(L):
@@ -195,3 +195,99 @@ class Integrator:
             self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), float(h), int(k), int(newton_max),
             ctypes.byref(info)))
         return info.as_dict()
+
+
+class Ensemble:
+    """Batched ensemble of independent problems (sphnse_ensemble)."""
+
+    def __init__(self, Ls, nus, Omega, device=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsphnse runs on a CUDA device; none is available")
+        self.device = torch.device(device if device is not None else "cuda")
+        lib = _capi.lib()
+        n = len(Ls)
+        Larr = (ctypes.c_int * n)(*[int(x) for x in Ls])
+        narr = (ctypes.c_double * n)(*[float(x) for x in nus])
+        with torch.cuda.device(self.device):
+            h = lib.sphnse_ensemble_create(n, Larr, narr, float(Omega))
+        if not h:
+            raise SphnseError("sphnse_ensemble_create", -1)
+        self._h = ctypes.c_void_p(h)
+        self.n = n
+        self.Ls = list(Ls)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.lib().sphnse_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, key, value):
+        check("sphnse_ensemble_set", _capi.lib().sphnse_ensemble_set(self._h, KEY[key], float(value)))
+
+    def _stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        check("sphnse_ensemble_set_stream", _capi.lib().sphnse_ensemble_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def _ptrs(self, i):
+        a, f, nc = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()
+        check("sphnse_ensemble_instance", _capi.lib().sphnse_ensemble_instance(
+            self._h, int(i), ctypes.byref(a), ctypes.byref(f), ctypes.byref(nc)))
+        return a.value, f.value, nc.value
+
+    def set_alpha(self, i, alpha):
+        """Copy a complex128 CUDA tensor into instance i's state."""
+        torch = _torch()
+        a, _, nc = self._ptrs(i)
+        if alpha.numel() != nc:
+            raise ValueError(f"instance {i} has {nc} coefficients")
+        src = alpha.to(self.device, torch.complex128).contiguous()
+        torch.cuda.current_stream(self.device).synchronize()
+        _cudart_copy(a, src.data_ptr(), nc * 16)
+
+    def get(self, i, which="alpha"):
+        """Copy of instance i's state ('alpha') or last RHS ('F')."""
+        torch = _torch()
+        a, f, nc = self._ptrs(i)
+        out = torch.empty(nc, dtype=torch.complex128, device=self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+        _cudart_copy(out.data_ptr(), a if which == "alpha" else f, nc * 16)
+        return out
+
+    def rhs(self):
+        self._stream()
+        check("sphnse_ensemble_rhs", _capi.lib().sphnse_ensemble_rhs(self._h))
+
+    def init(self, t0=0.0):
+        self._stream()
+        check("sphnse_ensemble_init", _capi.lib().sphnse_ensemble_init(self._h, float(t0)))
+
+    def step(self):
+        infos = (StepInfo * self.n)()
+        self._stream()
+        check("sphnse_ensemble_step", _capi.lib().sphnse_ensemble_step(self._h, ctypes.cast(infos, ctypes.c_void_p)))
+        return [x.as_dict() for x in infos]
+
+
+def _cudart_copy(dst, src, nbytes):
+    """Device-to-device copy of raw device memory through torch."""
+    torch = _torch()
+    src_t = _wrap(src, nbytes)
+    dst_t = _wrap(dst, nbytes)
+    dst_t.copy_(src_t)
+    torch.cuda.current_stream().synchronize()
+
+
+def _wrap(ptr, nbytes):
+    torch = _torch()
+    # a uint8 CUDA tensor view of raw device memory (CUDA array interface)
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (int(ptr), False), "version": 2}
+    return torch.as_tensor(_Holder(), device="cuda")

@@ -62,6 +62,15 @@ _SIGS = {
                                            ctypes.c_void_p, c_double_p]),
     "sphnse_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                         ctypes.c_double, c_double_p, ctypes.c_void_p]),
+    "sphnse_ensemble_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), c_double_p, ctypes.c_double]),
+    "sphnse_ensemble_destroy": (None, [ctypes.c_void_p]),
+    "sphnse_ensemble_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "sphnse_ensemble_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sphnse_ensemble_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int)]),
+    "sphnse_ensemble_rhs": (ctypes.c_int, [ctypes.c_void_p]),
+    "sphnse_ensemble_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "sphnse_ensemble_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sphnse_stage_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sphnse_stage_times": (ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.POINTER(ctypes.c_long)]),
     "sphnse_nu_sensitivity_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

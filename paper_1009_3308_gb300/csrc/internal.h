@@ -163,6 +163,15 @@ int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec);
 bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
 int launch_synthesis_tc(sphnse_plan* P);
+// batched FP32 passes over instances of one truncation (ensemble)
+int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride);
+int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
+                                  const float* bsyn, size_t sb, float* gsyn, size_t sg);
+int launch_ring_batch(sphnse_plan* P, int nb, const float* gsyn_r, size_t sgs, float* gana_r, size_t sga);
+int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
+                                 const float* gana, size_t sa, float* hana, size_t sh);
+int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstride, const double* alpha,
+                          double* out, const double* nu_inst);
 void tc_free(sphnse_plan* P);
 int launch_analysis_stream(sphnse_plan* P, int nfields, int prec);
 void stage_begin(sphnse_plan* P, int stage);

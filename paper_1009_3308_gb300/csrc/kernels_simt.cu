@@ -61,8 +61,12 @@ __global__ void k_prep(const double2* __restrict__ alpha, const double2* __restr
 // contracts in FP32 anyway), keeping the weak FP64 pipe for the state only.
 __global__ void __launch_bounds__(128) k_prep32(const double2* __restrict__ alpha, const double2* __restrict__ beta,
                                                 const float4* __restrict__ prepc, float* __restrict__ bsyn, int N,
-                                                int nf) {
+                                                int nf, int ncoef, size_t bstride) {
     __shared__ float2 sa[130], sb[130];
+    // batch of instances along gridDim.z (fixed strides between instances)
+    alpha += size_t(blockIdx.z) * ncoef;
+    if (beta) beta += size_t(blockIdx.z) * ncoef;
+    bsyn += size_t(blockIdx.z) * bstride;
     const int m = blockIdx.y, t = threadIdx.x;
     const int K0 = m + blockIdx.x * 128, K = K0 + t;
     const int lo = m > 0 ? m : 1;
@@ -271,9 +275,19 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
 // FP64.
 __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, const double2* __restrict__ alpha,
                            const double2* __restrict__ forcing, double2* __restrict__ out,
-                           const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n) {
+                           const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n,
+                           size_t hstride, const double* __restrict__ nu_inst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // batch of instances along gridDim.y: per-instance vectors, projections, nu
+    {
+        const size_t b = blockIdx.y;
+        hana += b * hstride;
+        alpha += b * n;
+        out += b * n;
+        if (forcing) forcing += b * n;
+        if (nu_inst) nu = nu_inst[b];
+    }
     const int L = lm[i].x, m = lm[i].y;
     const float4 c = finc[i];
     const float* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
@@ -330,7 +344,7 @@ int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int pre
     stage_begin(P, SPHNSE_STAGE_PREP);
     k_prep32<<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
                                          reinterpret_cast<const double2*>(beta), P->d_prepc32,
-                                         reinterpret_cast<float*>(P->d_bsyn), P->N, nf);
+                                         reinterpret_cast<float*>(P->d_bsyn), P->N, nf, P->n_coeff, 0);
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
@@ -398,7 +412,29 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
         k_finish32<<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const float*>(P->d_hana), nf,
                                                reinterpret_cast<const double2*>(alpha),
                                                reinterpret_cast<const double2*>(forcing),
-                                               reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n);
+                                               reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n, 0, nullptr);
+    stage_end(P, SPHNSE_STAGE_FINISH);
+    return check_cuda(cudaGetLastError());
+}
+
+// batched FP32 launchers over nb instances with fixed strides (ensemble)
+int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride) {
+    dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1, nb);
+    stage_begin(P, SPHNSE_STAGE_PREP);
+    k_prep32<<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha), nullptr, P->d_prepc32, bsyn,
+                                         P->N, 3, P->n_coeff, bstride);
+    stage_end(P, SPHNSE_STAGE_PREP);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstride, const double* alpha,
+                          double* out, const double* nu_inst) {
+    const int n = P->n_coeff;
+    dim3 blk(256), grd((n + 255) / 256, nb);
+    stage_begin(P, SPHNSE_STAGE_FINISH);
+    k_finish32<<<grd, blk, 0, P->stream>>>(0, hana, 2, reinterpret_cast<const double2*>(alpha), nullptr,
+                                           reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n,
+                                           hstride, nu_inst);
     stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }

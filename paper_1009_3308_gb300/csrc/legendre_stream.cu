@@ -53,6 +53,9 @@ struct StreamArgs {
     const int* item_off; // [gridDim + 1]
     unsigned* status;
     int N, nh, nlat;
+    // batches: an item v stands for instance v / (N+1) and order v % (N+1);
+    // per-instance strides (elements) of bsyn, gsyn, gana, hana
+    size_t sb, sg, sa, sh;
 };
 
 // chunk c of order m: rows [c HR, c HR + HR) of the even and of the odd block
@@ -71,7 +74,7 @@ __device__ void produce(const StreamArgs& a, T* stages, uint64_t* full, uint64_t
     const size_t rowb = size_t(a.nh) * sizeof(T);
     int it = 0;
     for (int ii = n_items_begin; ii < n_items_end; ++ii) {
-        const int m = a.items[ii];
+        const int m = a.items[ii] % (a.N + 1);
         const int ne = ext_even(a.N, m), no = ext_odd(a.N, m), e0 = ext_off(a.N, m);
         const int nch = ((ne > no ? ne : no) + HR - 1) / HR;
         for (int c = 0; c < nch; ++c, ++it) {
@@ -136,10 +139,12 @@ __global__ void __launch_bounds__(512, 1) k_syn_stream(StreamArgs a) {
     T* gsyn = reinterpret_cast<T*>(a.gsyn);
     int it = 0;
     for (int ii = ib; ii < iend; ++ii) {
-        const int m = a.items[ii];
+        const int inst = a.items[ii] / (N + 1), m = a.items[ii] % (N + 1);
         const int ne = ext_even(N, m), no = ext_odd(N, m), e0 = ext_off(N, m), cnt = ne + no;
         T* B = Bsm + size_t(ii & 1) * (N + 2) * 2 * NF;
-        for (int i = ct; i < cnt * 2 * NF; i += ncons) B[i] = bsyn[size_t(e0) * 2 * NF + i];
+        const T* bsrc = bsyn + inst * a.sb;
+        T* gdst = gsyn + inst * a.sg;
+        for (int i = ct; i < cnt * 2 * NF; i += ncons) B[i] = bsrc[size_t(e0) * 2 * NF + i];
         named_bar_sync(1, ncons);
         T acc[V][2 * NF];
 #pragma unroll
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(512, 1) k_syn_stream(StreamArgs a) {
                         if (f == 0) { o0 = gr; o1 = gi; }
                         else if (f == 1 || f == 3) { o0 = -mm * gi * inv_s; o1 = mm * gr * inv_s; }
                         else { o0 = -gr * inv_s; o1 = -gi * inv_s; }
-                        T* d = gsyn + ((size_t(f) * (N + 1) + m) * nlat + row) * 2;
+                        T* d = gdst + ((size_t(f) * (N + 1) + m) * nlat + row) * 2;
                         d[0] = o0;
                         d[1] = o1;
                     }
@@ -277,17 +282,19 @@ __global__ void __launch_bounds__(288, 1) k_ana_stream(StreamArgs a) {
     T* hana = reinterpret_cast<T*>(a.hana);
     int it = 0;
     for (int ii = ib; ii < iend; ++ii) {
-        const int m = a.items[ii];
+        const int inst = a.items[ii] / (N + 1), m = a.items[ii] % (N + 1);
         const int ne = ext_even(N, m), no = ext_odd(N, m), e0 = ext_off(N, m);
+        const T* gsrc = gana + inst * a.sa;
+        T* hdst = hana + inst * a.sh;
         // S is field-major: S[par][f][p] (par 0: G(p) + G(p'), 1: G(p) - G(p'))
         // so that a lane's V consecutive latitudes are one conflict-free vector load
         T* S = Ssm + size_t(ii & 1) * 2 * nh * 2 * NF;
         for (int i = ct; i < nh * NF; i += ncons) {
             const int f = i / nh, p = i % nh, pr = nlat - 1 - p;
-            const T* ga = gana + ((size_t(f) * (N + 1) + m) * nlat + p) * 2;
+            const T* ga = gsrc + ((size_t(f) * (N + 1) + m) * nlat + p) * 2;
             T ar = ga[0], ai = ga[1], br = T(0), bi = T(0);
             if (pr != p) {
-                const T* gb = gana + ((size_t(f) * (N + 1) + m) * nlat + pr) * 2;
+                const T* gb = gsrc + ((size_t(f) * (N + 1) + m) * nlat + pr) * 2;
                 br = gb[0];
                 bi = gb[1];
             }
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(288, 1) k_ana_stream(StreamArgs a) {
                 const bool writer = (NV == 32 || (lane & 1) == 0) && f < 2 * NF && r < nrow;
                 if (writer && !*abort) {
                     const int row = e0 + (par ? ne : 0) + c * HR + r0 + r;
-                    hana[size_t(row) * 2 * NF + f] = tot;
+                    hdst[size_t(row) * 2 * NF + f] = tot;
                 }
             }
             __syncwarp();
@@ -370,7 +377,7 @@ static int syn_stream_t(sphnse_plan* P) {
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_syn_stream<T, NF, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, P->d_bsyn, P->d_gsyn, nullptr, nullptr,
-                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat};
+                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     k_syn_stream<T, NF, HR><<<P->n_cta, threads, sm, P->stream>>>(a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
@@ -388,7 +395,7 @@ static int ana_stream_t(sphnse_plan* P) {
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_ana_stream<T, NF, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, nullptr, nullptr, P->d_gana, P->d_hana,
-                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat};
+                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     k_ana_stream<T, NF, HR, NTEAM><<<P->n_cta, threads, sm, P->stream>>>(a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
@@ -403,6 +410,43 @@ int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec) {
 int launch_analysis_stream(sphnse_plan* P, int nfields, int prec) {
     if (prec == SPHNSE_FP64) return nfields == 3 ? ana_stream_t<double, 3>(P) : ana_stream_t<double, 2>(P);
     return nfields == 3 ? ana_stream_t<float, 3>(P) : ana_stream_t<float, 2>(P);
+}
+
+// FP32 batched streaming passes over instances (items = inst * (N+1) + m)
+int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
+                                  const float* bsyn, size_t sb, float* gsyn, size_t sg) {
+    constexpr int HR = half_rows<float>();
+    constexpr int NST = nst<float>();
+    const int tpg = ((P->nh / 4 + 31) / 32) * 32;
+    const int threads = 32 + 2 * tpg;
+    const size_t sm = 128 + sizeof(float) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * (P->N + 2) * 6 +
+                                             size_t(P->nh) * 6);
+    if (threads > 512 || sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
+    cudaFuncSetAttribute(k_syn_stream<float, 3, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    StreamArgs a{P->tab[SPHNSE_FP32].syn, bsyn, gsyn, nullptr, nullptr, P->d_s, items, item_off, P->d_status,
+                 P->N, P->nh, P->nlat, sb, sg, 0, 0};
+    stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
+    k_syn_stream<float, 3, HR><<<ncta, threads, sm, P->stream>>>(a);
+    stage_end(P, SPHNSE_STAGE_SYNTHESIS);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
+                                 const float* gana, size_t sa, float* hana, size_t sh) {
+    constexpr int HR = half_rows<float>();
+    constexpr int QPS = 2 * HR / 4;
+    constexpr int NTEAM = 8 / QPS;
+    constexpr int NST = nst<float>();
+    const int threads = 32 + 32 * QPS * NTEAM;
+    const size_t sm = 128 + sizeof(float) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * 2 * P->nh * 4);
+    if (sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
+    cudaFuncSetAttribute(k_ana_stream<float, 2, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    StreamArgs a{P->tab[SPHNSE_FP32].syn, nullptr, nullptr, gana, hana, P->d_s, items, item_off, P->d_status,
+                 P->N, P->nh, P->nlat, 0, 0, sa, sh};
+    stage_begin(P, SPHNSE_STAGE_ANALYSIS);
+    k_ana_stream<float, 2, HR, NTEAM><<<ncta, threads, sm, P->stream>>>(a);
+    stage_end(P, SPHNSE_STAGE_ANALYSIS);
+    return check_cuda(cudaGetLastError());
 }
 
 }  // namespace sph

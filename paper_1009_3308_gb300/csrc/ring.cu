@@ -180,6 +180,7 @@ struct RingArgs {
     double* gout0;         // grid output rows (GRID)
     double* gout1;
     double* gout2;
+    size_t sgs, sga;       // per-instance strides (complex entries) along gridDim.y
 };
 
 template <typename T, typename TW, int MODE>
@@ -193,8 +194,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_ring(RingArgs a
     const int row = blockIdx.x;
     const int M = a.M, N = a.N, nlat = a.nlat;
     const size_t ld = size_t(N + 1);
-    const cx<T>* gs = reinterpret_cast<const cx<T>*>(a.gsyn);
-    cx<T>* ga = reinterpret_cast<cx<T>*>(a.gana);
+    const cx<T>* gs = reinterpret_cast<const cx<T>*>(a.gsyn) + size_t(blockIdx.y) * a.sgs;
+    cx<T>* ga = reinterpret_cast<cx<T>*>(a.gana) + size_t(blockIdx.y) * a.sga;
     auto G = [&](int f, int m) -> cx<T> { return gs[(size_t(f) * nlat + row) * ld + m]; };
 
     cx<T>* src[3] = {buf, buf + M, buf + 2 * M};
@@ -281,11 +282,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_ring(RingArgs a
 }
 
 template <typename T, typename TW, int MODE>
-static void ring_t(sphnse_plan* P, const RingArgs& a, const TW* tw, int threads) {
+static void ring_t(sphnse_plan* P, const RingArgs& a, const TW* tw, int threads, int nb = 1) {
     const int nbuf = MODE == RING_ADJOINT ? 3 : (MODE == RING_PROJECT ? 1 : 2);
     const size_t sm = size_t(nbuf) * P->nlon * sizeof(cx<T>) + size_t(P->nlon) * 2 * sizeof(T);
     cudaFuncSetAttribute(k_ring<T, TW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ring<T, TW, MODE><<<P->nlat, threads, sm, P->stream>>>(a, P->fft, tw);
+    k_ring<T, TW, MODE><<<dim3(P->nlat, nb), threads, sm, P->stream>>>(a, P->fft, tw);
+}
+
+// FP32 RHS ring pass over nb instances (latitude-major buffers with strides)
+int launch_ring_batch(sphnse_plan* P, int nb, const float* gsyn_r, size_t sgs, float* gana_r, size_t sga) {
+    RingArgs a{};
+    a.N = P->N;
+    a.M = P->nlon;
+    a.nlat = P->nlat;
+    a.mode = RING_RHS;
+    a.two_omega = 2.0 * P->Omega;
+    a.x = P->d_x;
+    a.s = P->d_s;
+    a.rw = P->d_rw;
+    a.gsyn = gsyn_r;
+    a.gana = gana_r;
+    a.sgs = sgs / 2;
+    a.sga = sga / 2;
+    int threads = ((P->nlon / 6 + 31) / 32) * 32;
+    if (threads < 32) threads = 32;
+    stage_begin(P, SPHNSE_STAGE_RING);
+    ring_t<float, float, RING_RHS>(P, a, P->d_tw32, threads, nb);
+    stage_end(P, SPHNSE_STAGE_RING);
+    return check_cuda(cudaGetLastError());
 }
 
 template <typename T, typename TW>
@@ -316,6 +340,7 @@ int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const do
     a.gout0 = gout0;
     a.gout1 = gout1;
     a.gout2 = gout2;
+    a.sgs = a.sga = 0;
     // in-place stages need blockDim >= M / 6 (at most 3 butterflies per thread)
     int threads = ((P->nlon / 6 + 31) / 32) * 32;
     if (threads < 32) threads = 32;
