@@ -188,6 +188,94 @@ def time_rhs(plan, a, out, steps, torch):
     return e0.elapsed_time(e1) / steps
 
 
+def _timed(fn, torch):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def extra_ndf_L511(torch, prec, nsteps=8):
+    """Adaptive NDF steps at the L = 511 workload (rtol 1e-6, mixed path)."""
+    from paper_1009_3308_gb300 import Integrator, Plan
+    from seeded_inputs import workload
+    w = workload("L511")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision=prec)
+    plan.set("RTOL", c["rtol"])
+    plan.set("ATOL", 1e-3 * c["rtol"] * float(abs(w["alpha0"]).max()))
+    integ = Integrator(plan, torch.from_numpy(w["alpha0"]).cuda())
+    integ.step()
+    infos, el = _timed(lambda: [integ.step() for _ in range(nsteps)], torch)
+    rhs = sum(i["rhs_evals"] for i in infos)
+    return {"steps_per_s": nsteps / el, "rhs_evals_per_step": rhs / nsteps, "steps": nsteps,
+            "precision": prec, "t_reached": integ.t}
+
+
+def extra_L31(torch, nsteps=100):
+    """The L = 31 workload: 100 adaptive FP64 steps, rtol 1e-8, steady forcing."""
+    from paper_1009_3308_gb300 import Integrator, Plan
+    from seeded_inputs import workload
+    w = workload("L31")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"])
+    plan.set("RTOL", c["rtol"])
+    plan.set("ATOL", 1e-3 * c["rtol"] * float(abs(w["alpha0"]).max()))
+    integ = Integrator(plan, torch.from_numpy(w["alpha0"]).cuda(), forcing=torch.from_numpy(w["forcing"]).cuda())
+    infos, el = _timed(lambda: [integ.step() for _ in range(nsteps)], torch)
+    rhs = sum(i["rhs_evals"] for i in infos)
+    return {"steps_per_s": nsteps / el, "rhs_per_s": rhs / el, "steps": nsteps, "t_reached": integ.t,
+            "precision": "fp64"}
+
+
+def extra_adjoint(torch, nsteps=40, checkpoint=20):
+    """Adjoint workload at L = 255: band energy + misfit gradient w.r.t. alpha0
+    and nu through frozen-controller NDF steps, FP32 contractions, FP64 state,
+    checkpoints every 20 steps."""
+    import math as _m
+    from paper_1009_3308_gb300 import Plan
+    from paper_1009_3308_gb300.adjoint import adaptive_schedule, objective, trajectory
+    from seeded_inputs import workload
+    w = workload("adjoint")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision="fp32")
+    plan.set("RTOL", c["rtol"])
+    plan.set("ATOL", 1e-3 * c["rtol"] * float(abs(w["alpha0"]).max()))
+    a0 = torch.from_numpy(w["alpha0"]).cuda()
+    tgt = torch.from_numpy(w["target"]).cuda()
+    _, sched, h0 = adaptive_schedule(plan, a0, nsteps)
+    a0r = torch.view_as_real(a0).clone().requires_grad_(True)
+    nut = torch.tensor(c["nu"], dtype=torch.float64, requires_grad=True)
+    J, tf = _timed(lambda: objective(plan, trajectory(plan, a0r, nut, sched, h0, checkpoint=checkpoint), tgt,
+                                     _m.radians(30), _m.radians(60)), torch)
+    _, tb = _timed(lambda: J.backward(), torch)
+    return {"adjoint_steps_per_s": nsteps / tb, "forward_replay_steps_per_s": nsteps / tf, "steps": nsteps,
+            "checkpoint": checkpoint, "precision": "fp32 contractions, fp64 state", "L": c["L"],
+            "grad_norm": float(a0r.grad.norm()), "dJ_dnu": float(nut.grad)}
+
+
+def extra_ensemble(torch, nsteps=3, n=256):
+    """Batched ensemble: 256 instances, L uniform over {63, 127, 255}, nu
+    log-uniform in [1e-5, 1e-3], per-instance adaptive steps (FP32 path)."""
+    from paper_1009_3308_gb300 import Ensemble
+    from seeded_inputs import ensemble
+    mem = ensemble(n)
+    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0)
+    for i, m in enumerate(mem):
+        ens.set_alpha(i, torch.from_numpy(m["alpha0"]))
+    ens.set("RTOL", 1e-6)
+    ens.set("ATOL", 1e-12)
+    ens.init(0.0)
+    ens.step()
+    _, tr = _timed(lambda: [ens.rhs() for _ in range(3)], torch)
+    infos, el = _timed(lambda: [ens.step() for _ in range(nsteps)], torch)
+    rhs = sum(sum(i["rhs_evals"] for i in inf) for inf in infos)
+    return {"instance_steps_per_s": n * nsteps / el, "instance_rhs_per_s_in_steps": rhs / el,
+            "batched_rhs_per_s": 3 / tr, "instance_rhs_per_s_batched": 3 * n / tr, "instances": n,
+            "steps": nsteps, "buckets": sorted(set(m["L"] for m in mem))}
+
+
 def cpu_baseline(w, target_s=15.0):
     """The FP64 oracle as it stands, on this host's cores: RHS evaluations at
     the benchmark workload (tables built first, not timed)."""
@@ -342,6 +430,12 @@ def main():
         extras["rel_err_vs_fp64"] = float(np.linalg.norm(fm - f64) / np.linalg.norm(f64))
         if "fp64" in extras:
             extras["speedup_vs_fp64"] = value / world / extras["fp64"]["rhs_per_s"]
+        for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)), ("adjoint_L255", lambda: extra_adjoint(torch)),
+                         ("ensemble", lambda: extra_ensemble(torch)), ("L31_fp64_steps", lambda: extra_L31(torch))):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # an extra must not hide the headline line
+                extras[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
