@@ -272,9 +272,13 @@ int sphnse_ensemble_step(sphnse_ensemble* ens, sphnse_step_info* info);
 #define SPHNSE_STAGE_TRANSPOSE  6  /* order-major <-> latitude-major transposes */
 #define SPHNSE_NSTAGES          7
 
-/* enable != 0: record a CUDA event pair on the plan's stream around every
- * later kernel launch, grouped by stage; enable == 0: stop and keep totals.
- * Enabling clears the totals. */
+#define SPHNSE_STAGE_ALL        (-1)
+
+/* enable = bit mask of stages (bit s = stage s; SPHNSE_STAGE_ALL for every
+ * stage): record a CUDA event pair on the plan's stream around every later
+ * kernel launch of an enabled stage; enable == 0: stop and keep totals.
+ * Enabling clears the totals.  Every event pair costs stream time, so a
+ * throughput measurement should enable only the stage it reports. */
 int sphnse_stage_timing(sphnse_plan* plan, int enable);
 
 /* Synchronise the plan's stream, fold the recorded events into totals and

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -19,6 +20,24 @@ __host__ __device__ inline int packed_index(int N, int m, int L) {
     return packed_off(N, m) + L - (m > 0 ? m : 1);
 }
 inline int n_packed(int N) { return (N + 1) * (N + 2) / 2 - 1; }
+// inverse of packed_index: (L, m) of packed entry i (m = 0 holds L = 1..N, then
+// order m >= 1 holds L = m..N from N + u (N+1) - u (u+1) / 2, u = m - 1)
+__host__ __device__ inline void packed_lm(int N, int i, int& L, int& m) {
+    if (i < N) {
+        m = 0;
+        L = i + 1;
+        return;
+    }
+    const int ip = i - N;
+    const float b = float(N) + 0.5f;
+    const float disc = b * b - 2.f * float(ip);
+    int u = int(b - sqrtf(disc > 0.f ? disc : 0.f));
+    auto off = [N](int v) { return v * (N + 1) - v * (v + 1) / 2; };
+    while (u > 0 && off(u) > ip) --u;
+    while (u < N && off(u + 1) <= ip) ++u;
+    m = u + 1;
+    L = ip - off(u) + m;
+}
 
 // Extended-degree ("ext") rows: for each m the degrees K = m..N+1 (n_m = N+2-m
 // of them), split by the parity of K - m: even rows first (K = m + 2j,
@@ -74,6 +93,8 @@ struct TcState {
     void* smap_lo = nullptr;
     void* tsyn_hi = nullptr;     // transposed padded bf16 tables [block][nh][pad8(n)]
     void* tsyn_lo = nullptr;
+    void* btiles = nullptr;      // synthesis B tiles [tile][16][64] bf16, swizzled (k_prep_tc)
+    int* tile_off = nullptr;     // first tile of block (m, parity)
     size_t tsyn_bytes = 0;
     bool syn_ready = false;
 };
@@ -100,6 +121,7 @@ struct sphnse_plan {
     double* d_rw = nullptr;      // (2 pi / M) w_p / sin(theta_p), nlat
     double* d_tw = nullptr;      // e^{-2 pi i t / M}, M complex (FP64)
     float* d_tw32 = nullptr;     // same in FP32
+    float* d_ftw = nullptr;      // four-step ring kernel twiddles (M = 24 M2), FP32
     int2* d_lm = nullptr;        // (L, m) of each packed entry
     double4_32a* d_prepc = nullptr;  // per ext row (m, K): (lam_K^{1/2}, lam_K^{-1/2}, c_down, c_up)
     float4* d_prepc32 = nullptr; // FP32 copies of the two coefficient tables
@@ -131,7 +153,7 @@ struct sphnse_plan {
     size_t work_bytes = 0;
 
     // optional per-stage CUDA-event timing on the plan's stream
-    bool timing = false;
+    unsigned timing = 0;         // bit mask of timed stages
     std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];
     int ev_used[SPHNSE_NSTAGES] = {0};
     double stage_ms[SPHNSE_NSTAGES] = {0};
@@ -163,11 +185,17 @@ int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec);
 bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
 int launch_synthesis_tc(sphnse_plan* P);
+int launch_prep_tc(sphnse_plan* P, const double* alpha);
 // batched FP32 passes over instances of one truncation (ensemble)
 int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride);
 int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
                                   const float* bsyn, size_t sb, float* gsyn, size_t sg);
 int launch_ring_batch(sphnse_plan* P, int nb, const float* gsyn_r, size_t sgs, float* gana_r, size_t sga);
+// four-step FP32 RHS ring kernel on the order-major buffers (M = 24 M2, M2 = 4..64, nlat even)
+int ring4_m2(int nlon, int nlat);
+bool ring4_ok(const sphnse_plan* P);
+std::vector<float> ring4_twiddles(int nlon);
+int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga);
 int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
                                  const float* gana, size_t sa, float* hana, size_t sh);
 int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstride, const double* alpha,
@@ -177,6 +205,24 @@ int launch_analysis_stream(sphnse_plan* P, int nfields, int prec);
 void stage_begin(sphnse_plan* P, int stage);
 void stage_end(sphnse_plan* P, int stage);
 int check_cuda(cudaError_t e);
+
+// Launch with programmatic stream serialisation (the kernel calls pdl_wait()
+// before it reads what its predecessor on the stream wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // whole pipelines
 int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, double* out);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace sph {
 
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(128) k_prep32(const double2* __restrict__ alph
                                                 const float4* __restrict__ prepc, float* __restrict__ bsyn, int N,
                                                 int nf, int ncoef, size_t bstride) {
     __shared__ float2 sa[130], sb[130];
+    pdl_launch();
     // batch of instances along gridDim.z (fixed strides between instances)
     alpha += size_t(blockIdx.z) * ncoef;
     if (beta) beta += size_t(blockIdx.z) * ncoef;
@@ -277,6 +279,8 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
                            const double2* __restrict__ forcing, double2* __restrict__ out,
                            const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n,
                            size_t hstride, const double* __restrict__ nu_inst) {
+    pdl_launch();
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     // batch of instances along gridDim.y: per-instance vectors, projections, nu
@@ -288,7 +292,9 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
         if (forcing) forcing += b * n;
         if (nu_inst) nu = nu_inst[b];
     }
-    const int L = lm[i].x, m = lm[i].y;
+    int L, m;
+    packed_lm(N, i, L, m);
+    (void)lm;
     const float4 c = finc[i];
     const float* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
     const float* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
@@ -409,10 +415,11 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
                                                      reinterpret_cast<const double2*>(forcing),
                                                      reinterpret_cast<double2*>(out), P->d_lm, P->d_finc, P->N, P->nu, n);
     else
-        k_finish32<<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const float*>(P->d_hana), nf,
-                                               reinterpret_cast<const double2*>(alpha),
-                                               reinterpret_cast<const double2*>(forcing),
-                                               reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n, 0, nullptr);
+        launch_pdl(k_finish32, grd, blk, 0, P->stream, kind, static_cast<const float*>(P->d_hana), nf,
+                   reinterpret_cast<const double2*>(alpha), reinterpret_cast<const double2*>(forcing),
+                   reinterpret_cast<double2*>(out), static_cast<const int2*>(P->d_lm),
+                   static_cast<const float4*>(P->d_finc32), P->N, P->nu, n, size_t(0),
+                   static_cast<const double*>(nullptr));
     stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }
@@ -432,9 +439,10 @@ int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstr
     const int n = P->n_coeff;
     dim3 blk(256), grd((n + 255) / 256, nb);
     stage_begin(P, SPHNSE_STAGE_FINISH);
-    k_finish32<<<grd, blk, 0, P->stream>>>(0, hana, 2, reinterpret_cast<const double2*>(alpha), nullptr,
-                                           reinterpret_cast<double2*>(out), P->d_lm, P->d_finc32, P->N, P->nu, n,
-                                           hstride, nu_inst);
+    launch_pdl(k_finish32, grd, blk, 0, P->stream, 0, hana, 2, reinterpret_cast<const double2*>(alpha),
+               static_cast<const double2*>(nullptr), reinterpret_cast<double2*>(out),
+               static_cast<const int2*>(P->d_lm), static_cast<const float4*>(P->d_finc32), P->N, P->nu, n, hstride,
+               nu_inst);
     stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }

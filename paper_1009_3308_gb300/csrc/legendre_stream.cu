@@ -125,11 +125,14 @@ __global__ void __launch_bounds__(512, 1) k_syn_stream(StreamArgs a) {
         fence_barrier_init();
     }
     __syncthreads();
+    pdl_launch();
     const int ib = a.item_off[blockIdx.x], iend = a.item_off[blockIdx.x + 1];
     if (threadIdx.x < 32) {
+        // the tables do not depend on the predecessor: stream them right away
         if (threadIdx.x == 0) produce<T, HR>(a, stages, full, empty, abort, ib, iend);
         return;
     }
+    pdl_wait();
     const int ct = threadIdx.x - 32;
     const int g = ct / tpg;               // 0: even rows, 1: odd rows
     const int p0 = (ct % tpg) * V;
@@ -268,11 +271,14 @@ __global__ void __launch_bounds__(288, 1) k_ana_stream(StreamArgs a) {
         fence_barrier_init();
     }
     __syncthreads();
+    pdl_launch();
     const int ib = a.item_off[blockIdx.x], iend = a.item_off[blockIdx.x + 1];
     if (threadIdx.x < 32) {
+        // the tables do not depend on the predecessor: stream them right away
         if (threadIdx.x == 0) produce<T, HR>(a, stages, full, empty, abort, ib, iend);
         return;
     }
+    pdl_wait();
     const int ct = threadIdx.x - 32, ncons = blockDim.x - 32;
     const int warp = ct / 32, lane = ct & 31;
     const int team = warp / QPS, q = warp % QPS;
@@ -379,7 +385,7 @@ static int syn_stream_t(sphnse_plan* P) {
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, P->d_bsyn, P->d_gsyn, nullptr, nullptr,
                  P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    k_syn_stream<T, NF, HR><<<P->n_cta, threads, sm, P->stream>>>(a);
+    launch_pdl(k_syn_stream<T, NF, HR>, dim3(P->n_cta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(cudaGetLastError());
 }
@@ -397,7 +403,7 @@ static int ana_stream_t(sphnse_plan* P) {
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, nullptr, nullptr, P->d_gana, P->d_hana,
                  P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
-    k_ana_stream<T, NF, HR, NTEAM><<<P->n_cta, threads, sm, P->stream>>>(a);
+    launch_pdl(k_ana_stream<T, NF, HR, NTEAM>, dim3(P->n_cta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
     return check_cuda(cudaGetLastError());
 }
@@ -426,7 +432,7 @@ int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* i
     StreamArgs a{P->tab[SPHNSE_FP32].syn, bsyn, gsyn, nullptr, nullptr, P->d_s, items, item_off, P->d_status,
                  P->N, P->nh, P->nlat, sb, sg, 0, 0};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    k_syn_stream<float, 3, HR><<<ncta, threads, sm, P->stream>>>(a);
+    launch_pdl(k_syn_stream<float, 3, HR>, dim3(ncta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(cudaGetLastError());
 }
@@ -444,7 +450,7 @@ int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* it
     StreamArgs a{P->tab[SPHNSE_FP32].syn, nullptr, nullptr, gana, hana, P->d_s, items, item_off, P->d_status,
                  P->N, P->nh, P->nlat, 0, 0, sa, sh};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
-    k_ana_stream<float, 2, HR, NTEAM><<<ncta, threads, sm, P->stream>>>(a);
+    launch_pdl(k_ana_stream<float, 2, HR, NTEAM>, dim3(ncta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
     return check_cuda(cudaGetLastError());
 }

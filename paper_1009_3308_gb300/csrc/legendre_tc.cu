@@ -1,22 +1,28 @@
-// Tensor-core (tcgen05) Legendre analysis with BF16 hi + lo split operands
-// and FP32 accumulation in tensor memory.
+// Tensor-core (tcgen05) Legendre synthesis and analysis with BF16 hi + lo
+// split operands and FP32 accumulation in tensor memory.
 //
-// The per-order analysis of the RHS (Sec. 4.2; the projection of Eq.
-// (disc_vec_orth_proj) after the longitude transform) is, per order m and
-// parity of K - m, the dense contraction
-//     H[K][c] = sum_p Pt_K^m(x_p) S[p][c],   p over the northern nodes,
-// with S the hemispheric sum / difference of the weighted Fourier profiles.
-// A = table rows (M = degrees, K = latitudes, K-major), B = S (N = columns).
-// Split precision: A = A_hi + A_lo, B = B_hi + B_lo (BF16 each), and
-//     D = A_hi [B_hi | B_lo] + A_lo [B_hi | 0]      (two MMAs per K step)
-// so that H = D[:, 0:c] + D[:, c:2c] = A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// Per order m and parity of K - m both Legendre steps of the RHS (Sec. 4.2:
+// the evaluation of Eq. (app_soln_rep) on the Gauss latitudes, and the
+// projection of Eq. (disc_vec_orth_proj) after the longitude transform) are
+// dense contractions with the table block Pt_K^m(x_p):
+//     synthesis  g[p][c] = sum_K Pt_K^m(x_p) b[K][c]
+//     analysis   H[K][c] = sum_p Pt_K^m(x_p) S[p][c]   (S = hemispheric sum / difference)
+// A = table tile (128 rows x 64 of the contracted index, K-major, 128-byte
+// swizzle, by TMA from one tensor map per (m, parity) block; rows past the
+// block come back zero-filled and are not read from HBM).  B = 16 x 64 tile
+// whose rows hold the hi parts (rows 0 .. 2F-1) and lo parts (rows 2F ..
+// 4F-1) of the F real columns.  Two MMAs per K step into two accumulators,
+//     D1 = A_hi B,   D2 = A_lo B,
+// give  result = D1[hi] + D1[lo] + D2[hi] + D2[lo]
+//              = A_hi B_hi + A_hi B_lo + A_lo B_hi + A_lo B_lo,
+// the product of the FP32-accurate split operands, accumulated in FP32.
 //
-// Tiles: 128 rows x 64 latitudes (one 128-byte swizzle atom column), loaded
-// by TMA from one tensor map per (m, parity) block; rows past the block come
-// back zero-filled from TMA and are not read from HBM.  B is written by the
-// CTA into the same swizzled K-major layout.  Warp roles per CTA: warp 0 TMA
-// producer, warp 1 MMA issuer (and TMEM owner), warps 2-5 B builders and
-// epilogue (tcgen05.ld of the 128 x 16 FP32 accumulator).
+// Synthesis: the B tiles are written ahead by k_prep_tc (one 2 KB tile per
+// (m, parity, K tile)) and arrive with every A stage by bulk copy; warp 0 is
+// the TMA producer, warp 1 issues the MMAs, warps 2-5 drain the accumulators.
+// Analysis: warps 2-5 build B from the weighted Fourier profiles in 16-byte
+// swizzle chunks, warps 6-9 drain the accumulators, so that neither stalls the
+// MMA issue behind the other.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -29,12 +35,39 @@
 
 namespace sph {
 
-constexpr int TC_NS = 4;          // A pipeline stages
+constexpr int TC_NS = 6;          // A pipeline stages
 constexpr int TC_TILE_M = 128;    // rows per MMA tile
 constexpr int TC_TILE_K = 64;     // K per smem tile (128 bytes of bf16)
 constexpr int TC_N = 16;          // accumulator columns (B rows)
 constexpr int TC_ATILE = TC_TILE_M * TC_TILE_K * 2;   // 16 KB
 constexpr int TC_BTILE = TC_N * TC_TILE_K * 2;        // 2 KB
+
+// 8 bf16 (hi or lo parts of v[0..7]) packed for one 16-byte swizzle chunk
+__device__ __forceinline__ uint4 pack_hi(const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ uint4 pack_lo(const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float a = v[2 * i], b = v[2 * i + 1];
+        const float la = a - __bfloat162float(__float2bfloat16_rn(a));
+        const float lb = b - __bfloat162float(__float2bfloat16_rn(b));
+        const __nv_bfloat162 l = __floats2bfloat162_rn(la, lb);
+        w[i] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+// byte offset of the 16-byte chunk q (K = 8q .. 8q+7) of row r in a swizzled tile
+__device__ __forceinline__ uint32_t sw128_chunk(int r, int q) {
+    return uint32_t(r) * 128u + (uint32_t(q ^ (r & 7)) << 4);
+}
 
 struct TcAnaArgs {
     const CUtensorMap* map_hi;   // per (m, parity) block, global memory
@@ -48,16 +81,15 @@ struct TcAnaArgs {
 };
 
 template <int NF>
-__global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
+__global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
     unsigned char* A_hi = smem;                                   // TC_NS x 16 KB
     unsigned char* A_lo = A_hi + TC_NS * TC_ATILE;                // TC_NS x 16 KB
-    unsigned char* B1 = A_lo + TC_NS * TC_ATILE;                  // 2 bufs x nkt x 2 KB
-    unsigned char* B2 = B1 + 2 * a.nkt * TC_BTILE;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(B2 + 2 * a.nkt * TC_BTILE);
+    unsigned char* Bt = A_lo + TC_NS * TC_ATILE;                  // 2 bufs x nkt x 2 KB
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bt + 2 * a.nkt * TC_BTILE);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + TC_NS;
     uint64_t* b_full = bars + 2 * TC_NS;
@@ -68,6 +100,11 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int N = a.N, nh = a.nh, nlat = a.nlat, nkt = a.nkt;
+    // rows 4 NF .. 15 of every B tile stay zero
+    for (int i = threadIdx.x; i < 2 * nkt * TC_BTILE / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(Bt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_NS; ++s) {
             mbar_init(&a_full[s], 1);
@@ -83,18 +120,19 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, 32);
+        tmem_alloc(tmem_slot, 64);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    pdl_launch();
     const uint32_t tmem = *tmem_slot;
     const int ib = a.item_off[blockIdx.x], nI = a.item_off[blockIdx.x + 1] - ib;
-    const int N = a.N, nh = a.nh, nlat = a.nlat, nkt = a.nkt;
 
     if (warp == 0) {
         if (lane == 0) {
+            // the tables do not depend on the predecessor: stream them right away
             const uint64_t pol = policy_evict_first();
             int it = 0;
             for (int i = 0; i < nI; ++i) {
@@ -120,20 +158,18 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
                 bool ok = mbar_wait(&b_full[buf], use & 1, abort, a.status);
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status) && ok;
                 tc_fence_after();
-                const uint32_t d = tmem + uint32_t(buf * TC_N);
+                const uint32_t d1 = tmem + uint32_t(buf * 2 * TC_N), d2 = d1 + TC_N;
                 for (int kt = 0; kt < nkt; ++kt, ++it) {
                     const int s = it % TC_NS;
                     const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
                     tc_fence_after();
                     if (ok && okA && !*abort) {
+                        const unsigned char* bt = Bt + (buf * nkt + kt) * TC_BTILE;
 #pragma unroll
                         for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
-                            const uint64_t ah = sdesc_sw128(A_hi + s * TC_ATILE + kk * 32);
-                            const uint64_t al = sdesc_sw128(A_lo + s * TC_ATILE + kk * 32);
-                            const uint64_t b1 = sdesc_sw128(B1 + (buf * nkt + kt) * TC_BTILE + kk * 32);
-                            const uint64_t b2 = sdesc_sw128(B2 + (buf * nkt + kt) * TC_BTILE + kk * 32);
-                            mma_bf16(d, ah, b1, idesc, (kt | kk) != 0);
-                            mma_bf16(d, al, b2, idesc, 1);
+                            const uint64_t bd = sdesc_sw128(bt + kk * 32);
+                            mma_bf16(d1, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d2, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
                         }
                     }
                     mma_commit(&a_empty[s]);
@@ -143,61 +179,72 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
             }
             if (nI > 0) mbar_wait(&acc_full[(nI - 1) & 1], ((nI - 1) >> 1) & 1, abort, a.status);
         }
-    } else {
-        // helpers: build B for item i, then drain the accumulator of item i-1
+    } else if (warp < 6) {
+        // B builders: task (K tile, chunk q of 8 latitudes, field f)
+        pdl_wait();
         const int ht = threadIdx.x - 64;
-        const int quarter = warp & 3;
-        const float* gana = a.gana;
-        auto build_B = [&](int i) {
+        const size_t ld = size_t(N + 1);
+        for (int i = 0; i < nI; ++i) {
+            const int buf = i & 1;
+            if (i >= 2) mbar_wait(&b_empty[buf], ((i >> 1) - 1) & 1, abort, a.status);
             const int4 itm = a.items[ib + i];
-            const int m = itm.y, par = itm.z, buf = i & 1;
-            const size_t ld = size_t(N + 1);
-            for (int p = ht; p < nkt * TC_TILE_K; p += 128) {
-                float v[2 * NF];
+            const int m = itm.y, par = itm.z;
+            for (int task = ht; task < nkt * 8 * NF; task += 128) {
+                const int f = task % NF, q = (task / NF) & 7, kt = task / (8 * NF);
+                const int p0 = kt * TC_TILE_K + q * 8;
+                const float* g = a.gana + (size_t(f) * ld + m) * size_t(nlat) * 2;
+                float nv[16], sv[16];
+                if (p0 + 8 <= nh) {
+                    const float4* gn = reinterpret_cast<const float4*>(g + size_t(p0) * 2);
+                    const float4* gs = reinterpret_cast<const float4*>(g + size_t(nlat - 8 - p0) * 2);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-                    if (p < nh) {
-                        const float* ga = gana + ((size_t(f) * ld + m) * nlat + p) * 2;
-                        ar = ga[0];
-                        ai = ga[1];
-                        const int pr = nlat - 1 - p;
-                        if (pr != p) {
-                            const float* gb = gana + ((size_t(f) * ld + m) * nlat + pr) * 2;
-                            br = gb[0];
-                            bi = gb[1];
-                        }
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 x = gn[u], y = gs[u];
+                        nv[4 * u] = x.x; nv[4 * u + 1] = x.y; nv[4 * u + 2] = x.z; nv[4 * u + 3] = x.w;
+                        sv[4 * u] = y.x; sv[4 * u + 1] = y.y; sv[4 * u + 2] = y.z; sv[4 * u + 3] = y.w;
                     }
-                    v[2 * f] = par ? ar - br : ar + br;
-                    v[2 * f + 1] = par ? ai - bi : ai + bi;
-                }
-                const int kt = p / TC_TILE_K, kl = p % TC_TILE_K;
-                unsigned char* t1 = B1 + (buf * nkt + kt) * TC_BTILE;
-                unsigned char* t2 = B2 + (buf * nkt + kt) * TC_BTILE;
+                } else {
 #pragma unroll
-                for (int n = 0; n < TC_N; ++n) {
-                    __nv_bfloat16 x1 = __float2bfloat16_rn(0.f), x2 = x1;
-                    if (n < 2 * NF) {
-                        x1 = __float2bfloat16_rn(v[n]);
-                        x2 = x1;
-                    } else if (n < 4 * NF) {
-                        const float hv = v[n - 2 * NF];
-                        x1 = __float2bfloat16_rn(hv - __bfloat162float(__float2bfloat16_rn(hv)));
+                    for (int e = 0; e < 8; ++e) {
+                        const int p = p0 + e, pr = nlat - 8 - p0 + e;
+                        const bool in = p < nh;
+                        nv[2 * e] = in ? g[2 * size_t(p)] : 0.f;
+                        nv[2 * e + 1] = in ? g[2 * size_t(p) + 1] : 0.f;
+                        const bool ins = (nlat - 1 - pr) < nh && pr >= 0;
+                        sv[2 * e] = ins ? g[2 * size_t(pr)] : 0.f;
+                        sv[2 * e + 1] = ins ? g[2 * size_t(pr) + 1] : 0.f;
                     }
-                    *reinterpret_cast<__nv_bfloat16*>(t1 + sw128_offset(n, kl)) = x1;
-                    *reinterpret_cast<__nv_bfloat16*>(t2 + sw128_offset(n, kl)) = x2;
                 }
+                // latitude p0 + e pairs with its mirror nlat - 1 - p0 - e = sv entry 7 - e
+                float re[8], im[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float sr = sv[2 * (7 - e)], si = sv[2 * (7 - e) + 1];
+                    re[e] = par ? nv[2 * e] - sr : nv[2 * e] + sr;
+                    im[e] = par ? nv[2 * e + 1] - si : nv[2 * e + 1] + si;
+                }
+                unsigned char* tile = Bt + (buf * nkt + kt) * TC_BTILE;
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f, q)) = pack_hi(re);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f + 1, q)) = pack_hi(im);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * NF + 2 * f, q)) = pack_lo(re);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * NF + 2 * f + 1, q)) = pack_lo(im);
             }
             fence_proxy_async_smem();
             mbar_arrive(&b_full[buf]);
-        };
-        auto epilogue = [&](int i) {
+        }
+    } else {
+        // epilogue: TMEM lanes of this warp's quarter -> projection rows
+        pdl_wait();
+        const int quarter = warp & 3;
+        for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
             const int m = itm.y, par = itm.z, t = itm.w, buf = i & 1;
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
-            float v[16];
-            tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * TC_N), v);
+            float v1[16], v2[16];
+            const uint32_t ta = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * 2 * TC_N);
+            tmem_ld16(ta, v1);
+            tmem_ld16(ta + TC_N, v2);
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
             const int ne = ext_even(N, m), no = ext_odd(N, m);
@@ -206,21 +253,16 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
             if (ok && r < nrows && !*abort) {
                 const int row = ext_off(N, m) + (par ? ne : 0) + r;
 #pragma unroll
-                for (int f = 0; f < 2 * NF; ++f) a.hana[size_t(row) * 2 * NF + f] = v[f] + v[2 * NF + f];
+                for (int c = 0; c < 2 * NF; ++c)
+                    a.hana[size_t(row) * 2 * NF + c] = (v1[c] + v1[2 * NF + c]) + (v2[c] + v2[2 * NF + c]);
             }
-        };
-        for (int i = 0; i < nI; ++i) {
-            if (i >= 2) mbar_wait(&b_empty[i & 1], ((i >> 1) - 1) & 1, abort, a.status);
-            build_B(i);
-            if (i >= 1) epilogue(i - 1);
         }
-        if (nI > 0) epilogue(nI - 1);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 32);
+        tmem_dealloc(tmem, 64);
     }
 }
 
@@ -230,41 +272,45 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc(TcAnaArgs a) {
 // Per order m and parity: g[p][c] = sum_j Pt_{K_j}^m(x_p) b[j][c], the dense
 // contraction with A = the transposed table block [nh][pad8(n_par)] (M =
 // latitudes, K = degrees, K-major; TMA zero-fills degrees past the block),
-// B = the coefficient sets of the three fields (N = 16: hi/lo columns as in
-// the analysis).  Both parities of an order go to separate accumulators so
-// that the epilogue forms north = E + O, south = E - O directly.
+// B = the prepacked coefficient tile of the three fields.  Both parities of
+// an order go to separate accumulators so that the epilogue forms north =
+// E + O, south = E - O directly.
 
 struct TcSynArgs {
     const CUtensorMap* map_hi;   // per (m, parity) block of the transposed tables
     const CUtensorMap* map_lo;
     const int* items;            // orders m per CTA (LPT)
     const int* item_off;
-    const float* bsyn;           // [n_ext][6]
+    const unsigned char* btiles; // [tile][16][64] bf16, 128-byte swizzle (k_prep_tc)
+    const int* tile_off;         // first tile of block b = 2 m + parity
     float* gsyn;                 // [3][N+1][nlat] complex (m-major)
     const double* sinth;
     unsigned* status;
-    int N, nh, nlat, nmt, maxkt;
+    int N, nh, nlat, nmt;
 };
 
-constexpr int TC_SYN_COLS = 256;  // TMEM columns: 2 buffers x 2 parities x nmt (<= 4) x 16
+constexpr int TC_SYN_COLS = 512;  // TMEM columns: 2 buffers x 2 parities x nmt (<= 4) x 2 x 16
+constexpr int TC_SYN_STAGE = 2 * TC_ATILE + TC_BTILE;
+
+__host__ __device__ inline int syn_nkt(int N, int m, int par) {
+    const int n = par ? ext_odd(N, m) : ext_even(N, m);
+    return (((n + 7) / 8) * 8 + TC_TILE_K - 1) / TC_TILE_K;
+}
 
 __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    const int maxkt = a.maxkt, nmt = a.nmt;
+    const int nmt = a.nmt;
     unsigned char* A_hi = smem;
     unsigned char* A_lo = A_hi + TC_NS * TC_ATILE;
-    unsigned char* B1 = A_lo + TC_NS * TC_ATILE;                 // [buf][par][kt] x 2 KB
-    unsigned char* B2 = B1 + 2 * 2 * maxkt * TC_BTILE;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(B2 + 2 * 2 * maxkt * TC_BTILE);
+    unsigned char* Bs = A_lo + TC_NS * TC_ATILE;                 // TC_NS x 2 KB
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + TC_NS * TC_BTILE);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + TC_NS;
-    uint64_t* b_full = bars + 2 * TC_NS;
-    uint64_t* b_empty = b_full + 2;
-    uint64_t* acc_full = b_full + 4;
-    uint64_t* acc_empty = b_full + 6;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 8);
+    uint64_t* acc_full = bars + 2 * TC_NS;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -273,8 +319,6 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             mbar_init(&a_empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&b_full[b], 128);
-            mbar_init(&b_empty[b], 1);
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
         }
@@ -291,28 +335,29 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     const uint32_t tmem = *tmem_slot;
     const int ib = a.item_off[blockIdx.x], nI = a.item_off[blockIdx.x + 1] - ib;
     const int N = a.N, nh = a.nh, nlat = a.nlat;
-    auto nkt_of = [&](int m, int par) {
-        const int n = par ? ext_odd(N, m) : ext_even(N, m);
-        return (((n + 7) / 8) * 8 + TC_TILE_K - 1) / TC_TILE_K;
-    };
+    pdl_launch();
 
     if (warp == 0) {
         if (lane == 0) {
+            pdl_wait();
             const uint64_t pol = policy_evict_first();
+            const uint64_t polb = policy_evict_last();
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int m = a.items[ib + i];
                 for (int par = 0; par < 2; ++par) {
-                    const int b = 2 * m + par, nkt = nkt_of(m, par);
+                    const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
+                    const unsigned char* bsrc = a.btiles + size_t(a.tile_off[b]) * TC_BTILE;
                     for (int kt = 0; kt < nkt; ++kt)
                         for (int mt = 0; mt < nmt; ++mt, ++it) {
                             const int s = it % TC_NS;
                             if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status))
                                 continue;
                             if (*abort) continue;
-                            mbar_arrive_expect_tx(&a_full[s], 2 * TC_ATILE);
+                            mbar_arrive_expect_tx(&a_full[s], TC_SYN_STAGE);
                             tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
                             tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                            bulk_g2s(Bs + s * TC_BTILE, bsrc + size_t(kt) * TC_BTILE, TC_BTILE, &a_full[s], polb);
                         }
                 }
             }
@@ -326,89 +371,60 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             for (int i = 0; i < nI; ++i) {
                 const int m = a.items[ib + i];
                 const int buf = i & 1, use = i >> 1;
-                bool ok = mbar_wait(&b_full[buf], use & 1, abort, a.status);
-                if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status) && ok;
+                bool ok = true;
+                if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
-                    const int nkt = nkt_of(m, par);
+                    const int nkt = syn_nkt(N, m, par);
                     for (int kt = 0; kt < nkt; ++kt)
                         for (int mt = 0; mt < nmt; ++mt, ++it) {
                             const int s = it % TC_NS;
                             const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
                             tc_fence_after();
-                            const uint32_t d = tmem + uint32_t(((buf * 2 + par) * nmt + mt) * TC_N);
+                            const uint32_t d = tmem + uint32_t(((buf * 2 + par) * nmt + mt) * 2 * TC_N);
                             if (ok && okA && !*abort) {
-                                const unsigned char* bt1 = B1 + ((buf * 2 + par) * maxkt + kt) * TC_BTILE;
-                                const unsigned char* bt2 = B2 + ((buf * 2 + par) * maxkt + kt) * TC_BTILE;
 #pragma unroll
                                 for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
-                                    mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), sdesc_sw128(bt1 + kk * 32),
-                                             idesc, (kt | kk) != 0);
-                                    mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), sdesc_sw128(bt2 + kk * 32),
-                                             idesc, 1);
+                                    const uint64_t bd = sdesc_sw128(Bs + s * TC_BTILE + kk * 32);
+                                    mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                                    mma_bf16(d + TC_N, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc,
+                                             (kt | kk) != 0);
                                 }
                             }
                             mma_commit(&a_empty[s]);
                         }
                 }
                 mma_commit(&acc_full[buf]);
-                mma_commit(&b_empty[buf]);
             }
             if (nI > 0) mbar_wait(&acc_full[(nI - 1) & 1], ((nI - 1) >> 1) & 1, abort, a.status);
         }
     } else {
-        const int ht = threadIdx.x - 64;
+        pdl_wait();
         const int quarter = warp & 3;
-        auto build_B = [&](int i) {
-            const int m = a.items[ib + i], buf = i & 1;
-            const int ne = ext_even(N, m), e0 = ext_off(N, m);
-            for (int par = 0; par < 2; ++par) {
-                const int n = par ? ext_odd(N, m) : ne;
-                const int nk = nkt_of(m, par) * TC_TILE_K;
-                for (int j = ht; j < nk; j += 128) {
-                    float v[6];
-                    if (j < n) {
-                        const float* src = a.bsyn + size_t(e0 + (par ? ne : 0) + j) * 6;
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) v[c] = src[c];
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) v[c] = 0.f;
-                    }
-                    const int kt = j / TC_TILE_K, kl = j % TC_TILE_K;
-                    unsigned char* t1 = B1 + ((buf * 2 + par) * maxkt + kt) * TC_BTILE;
-                    unsigned char* t2 = B2 + ((buf * 2 + par) * maxkt + kt) * TC_BTILE;
-#pragma unroll
-                    for (int c = 0; c < TC_N; ++c) {
-                        __nv_bfloat16 x1 = __float2bfloat16_rn(0.f), x2 = x1;
-                        if (c < 6) {
-                            x1 = __float2bfloat16_rn(v[c]);
-                            x2 = x1;
-                        } else if (c < 12) {
-                            x1 = __float2bfloat16_rn(v[c - 6] - __bfloat162float(__float2bfloat16_rn(v[c - 6])));
-                        }
-                        *reinterpret_cast<__nv_bfloat16*>(t1 + sw128_offset(c, kl)) = x1;
-                        *reinterpret_cast<__nv_bfloat16*>(t2 + sw128_offset(c, kl)) = x2;
-                    }
-                }
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&b_full[buf]);
-        };
-        auto epilogue = [&](int i) {
+        const size_t ld = size_t(N + 1);
+        for (int i = 0; i < nI; ++i) {
             const int m = a.items[ib + i], buf = i & 1;
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
             const float mm = float(m);
-            const size_t ld = size_t(N + 1);
             for (int mt = 0; mt < nmt; ++mt) {
-                float E[16], O[16];
+                float e1[16], e2[16], o1[16], o2[16];
                 const uint32_t lanes = uint32_t(quarter * 32) << 16;
-                tmem_ld16(tmem + lanes + uint32_t(((buf * 2 + 0) * nmt + mt) * TC_N), E);
-                tmem_ld16(tmem + lanes + uint32_t(((buf * 2 + 1) * nmt + mt) * TC_N), O);
+                const uint32_t ce = uint32_t(((buf * 2 + 0) * nmt + mt) * 2 * TC_N);
+                const uint32_t co = uint32_t(((buf * 2 + 1) * nmt + mt) * 2 * TC_N);
+                tmem_ld16(tmem + lanes + ce, e1);
+                tmem_ld16(tmem + lanes + ce + TC_N, e2);
+                tmem_ld16(tmem + lanes + co, o1);
+                tmem_ld16(tmem + lanes + co + TC_N, o2);
                 const int p = mt * TC_TILE_M + quarter * 32 + lane;
                 if (!ok || p >= nh || *abort) continue;
                 const float inv_s = float(1.0 / a.sinth[p]);
+                float E[6], O[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    E[c] = (e1[c] + e1[6 + c]) + (e2[c] + e2[6 + c]);
+                    O[c] = (o1[c] + o1[6 + c]) + (o2[c] + o2[6 + c]);
+                }
 #pragma unroll
                 for (int hemi = 0; hemi < 2; ++hemi) {
                     const int row = hemi == 0 ? p : nlat - 1 - p;
@@ -416,27 +432,19 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                     const float sg = hemi == 0 ? 1.f : -1.f;
 #pragma unroll
                     for (int f = 0; f < 3; ++f) {
-                        const float gr = (E[2 * f] + E[6 + 2 * f]) + sg * (O[2 * f] + O[6 + 2 * f]);
-                        const float gi = (E[2 * f + 1] + E[7 + 2 * f]) + sg * (O[2 * f + 1] + O[7 + 2 * f]);
-                        float o0, o1;
-                        if (f == 0) { o0 = gr; o1 = gi; }
-                        else if (f == 1) { o0 = -mm * gi * inv_s; o1 = mm * gr * inv_s; }
-                        else { o0 = -gr * inv_s; o1 = -gi * inv_s; }
-                        float* d = a.gsyn + ((size_t(f) * ld + m) * nlat + row) * 2;
-                        d[0] = o0;
-                        d[1] = o1;
+                        const float gr = E[2 * f] + sg * O[2 * f];
+                        const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
+                        float2 o;
+                        if (f == 0) o = make_float2(gr, gi);
+                        else if (f == 1) o = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
+                        else o = make_float2(-gr * inv_s, -gi * inv_s);
+                        reinterpret_cast<float2*>(a.gsyn)[(size_t(f) * ld + m) * nlat + row] = o;
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
-        };
-        for (int i = 0; i < nI; ++i) {
-            if (i >= 2) mbar_wait(&b_empty[i & 1], ((i >> 1) - 1) & 1, abort, a.status);
-            build_B(i);
-            if (i >= 1) epilogue(i - 1);
         }
-        if (nI > 0) epilogue(nI - 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -444,6 +452,51 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         tc_fence_after();
         tmem_dealloc(tmem, TC_SYN_COLS);
     }
+}
+
+// Coefficient sets of the synthesis (zeta: lam^{1/2} a_K; theta: lam^{-1/2}
+// a_K; phi: c_down a_{K-1} + c_up a_{K+1}, the degree-shift form of
+// sin(theta) d/dtheta), written as the B tiles of k_syn_tc: thread (K tile
+// kt, chunk q, column c) of block b = (m, parity) computes column c for the 8
+// degrees K = m + par + 2 j, j = 64 kt + 8 q .. +7, and stores its hi part in
+// row c and its lo part in row 6 + c (rows 12-15 stay zero).
+__global__ void __launch_bounds__(384) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
+                                                 unsigned char* __restrict__ btiles, const int* __restrict__ tile_off,
+                                                 int N) {
+    pdl_launch();
+    const int b = blockIdx.x, m = b >> 1, par = b & 1;
+    const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
+    const int kt = threadIdx.x >> 3, q = threadIdx.x & 7, c = threadIdx.y;
+    if (kt >= syn_nkt(N, m, par)) return;
+    const int j0 = kt * TC_TILE_K + q * 8;
+    const int lo = m > 0 ? m : 1;
+    const int K0 = m + par + 2 * j0;
+    const int pk = packed_off(N, m) - lo;   // packed index of degree K is pk + K
+    const int r0 = ext_off(N, m) + (par ? ne : 0);
+    const bool shift = c >= 4;              // phi column: neighbours K - 1, K + 1
+    const bool im = c & 1;
+    float w[9];                             // alpha parts at K (8) or at K - 1 + 2 e (9)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const int K = shift ? K0 - 1 + 2 * e : K0 + 2 * e;
+        float v = 0.f;
+        if ((shift || e < 8) && K >= lo && K <= N) {
+            const double2 a = alpha[pk + K];
+            v = float(im ? a.y : a.x);
+        }
+        w[e] = v;
+    }
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = j0 + e;
+        float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < n) cf = prepc[r0 + j];
+        v[e] = c < 2 ? cf.x * w[e] : c < 4 ? cf.y * w[e] : fmaf(cf.z, w[e], cf.w * w[e + 1]);
+    }
+    unsigned char* tile = btiles + size_t(tile_off[b] + kt) * TC_BTILE;
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(c, q)) = pack_hi(v);
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(6 + c, q)) = pack_lo(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -542,16 +595,16 @@ int tc_setup_analysis(sphnse_plan* P) {
 template <int NF>
 static int ana_tc_t(sphnse_plan* P) {
     const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
-    const size_t sm = 1024 + 2 * size_t(TC_NS) * TC_ATILE + 4 * size_t(nkt) * TC_BTILE + 256;
-    if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
+    const size_t sm = 1024 + 2 * size_t(TC_NS) * TC_ATILE + 2 * size_t(nkt) * TC_BTILE + 256;
+    if (sm > 227 * 1024 || 4 * NF > TC_N) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_ana_tc<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     TcAnaArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi), reinterpret_cast<const CUtensorMap*>(P->tc.map_lo), P->tc.ana_items, P->tc.ana_off,
                 reinterpret_cast<const float*>(P->d_gana), reinterpret_cast<float*>(P->d_hana), P->d_status,
                 P->N, P->nh, P->nlat, nkt};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
-    k_ana_tc<NF><<<P->tc.ana_cta, 192, sm, P->stream>>>(a);
+    const cudaError_t e = launch_pdl(k_ana_tc<NF>, dim3(P->tc.ana_cta), dim3(320), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 
 int launch_analysis_tc(sphnse_plan* P, int nfields) {
@@ -619,8 +672,27 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemcpy(T.smap_hi, mh.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     cudaMemcpy(T.smap_lo, ml.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    // B tiles of the coefficient sets (k_prep_tc): one 2 KB tile per (m, parity, K tile)
+    std::vector<int> toff(nblk + 1, 0);
+    for (int b = 0; b < nblk; ++b) toff[b + 1] = toff[b] + syn_nkt(N, b / 2, b % 2);
+    if (cudaMalloc(&T.btiles, size_t(toff[nblk]) * TC_BTILE) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.tile_off), toff.size() * sizeof(int)) != cudaSuccess)
+        return SPHNSE_E_NOMEM;
+    cudaMemset(T.btiles, 0, size_t(toff[nblk]) * TC_BTILE);
+    cudaMemcpy(T.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
     T.tsyn_bytes = 2 * total * 2;
     T.syn_ready = true;
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_prep_tc(sphnse_plan* P, const double* alpha) {
+    int rc = tc_setup_synthesis(P);
+    if (rc) return rc;
+    if (syn_nkt(P->N, 0, 0) * 8 > 64) return SPHNSE_E_UNSUPPORTED;
+    stage_begin(P, SPHNSE_STAGE_PREP);
+    k_prep_tc<<<2 * (P->N + 1), dim3(64, 6), 0, P->stream>>>(reinterpret_cast<const double2*>(alpha), P->d_prepc32,
+                                                     static_cast<unsigned char*>(P->tc.btiles), P->tc.tile_off, P->N);
+    stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
 
@@ -629,23 +701,23 @@ int launch_synthesis_tc(sphnse_plan* P) {
     if (rc) return rc;
     const int nmt = (P->nh + TC_TILE_M - 1) / TC_TILE_M;
     if (nmt > 4) return SPHNSE_E_UNSUPPORTED;
-    const int maxkt = (((ext_even(P->N, 0) + 7) / 8) * 8 + TC_TILE_K - 1) / TC_TILE_K;
-    const size_t sm = 1024 + 2 * size_t(TC_NS) * TC_ATILE + 8 * size_t(maxkt) * TC_BTILE + 256;
+    const size_t sm = 1024 + size_t(TC_NS) * TC_SYN_STAGE + 256;
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->d_items, P->d_item_off,
-                reinterpret_cast<const float*>(P->d_bsyn), reinterpret_cast<float*>(P->d_gsyn), P->d_s,
-                P->d_status, P->N, P->nh, P->nlat, nmt, maxkt};
+                static_cast<const unsigned char*>(P->tc.btiles), P->tc.tile_off, reinterpret_cast<float*>(P->d_gsyn),
+                P->d_s, P->d_status, P->N, P->nh, P->nlat, nmt};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    k_syn_tc<<<P->n_cta, 192, sm, P->stream>>>(a);
+    const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->n_cta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
-    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.smap_hi, T.smap_lo, T.tsyn_hi, T.tsyn_lo};
+    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.smap_hi, T.smap_lo, T.tsyn_hi, T.tsyn_lo, T.btiles,
+                    T.tile_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = TcState();

@@ -43,10 +43,10 @@ static void record_stage_event(sphnse_plan* P, int stage) {
 }
 
 void stage_begin(sphnse_plan* P, int stage) {
-    if (P->timing) record_stage_event(P, stage);
+    if (P->timing & (1u << stage)) record_stage_event(P, stage);
 }
 void stage_end(sphnse_plan* P, int stage) {
-    if (P->timing) record_stage_event(P, stage);
+    if (P->timing & (1u << stage)) record_stage_event(P, stage);
 }
 
 static void free_tables(Tables& t) {
@@ -120,11 +120,16 @@ int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, doubl
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
     int rc;
     const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
-    if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
+    if ((rc = tc ? launch_prep_tc(P, alpha) : launch_prep(P, alpha, nullptr, prec))) return rc;
     if ((rc = tc ? launch_synthesis_tc(P) : launch_synthesis(P, 3, prec))) return rc;
-    if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
-    if ((rc = launch_ring(P, RING_RHS, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
-    if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
+    if (prec == SPHNSE_FP32 && ring4_ok(P)) {
+        if ((rc = launch_ring4(P, 1, static_cast<const float*>(P->d_gsyn), 0, static_cast<float*>(P->d_gana), 0)))
+            return rc;
+    } else {
+        if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
+        if ((rc = launch_ring(P, RING_RHS, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
+        if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
+    }
     if ((rc = tc ? launch_analysis_tc(P, 2) : launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 0, prec, alpha, forcing, out);
 }
@@ -157,7 +162,7 @@ static void destroy_plan(sphnse_plan* P) {
     for (auto& t : P->tab) free_tables(t);
     tc_free(P);
     void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
-                    P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
+                    P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_ftw, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
                     P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -278,6 +283,8 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     if (!rc) rc = dalloc(&P->d_rw, nlat * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tw, tw.size() * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tw32, tw32.size() * sizeof(float));
+    const std::vector<float> ftw = ring4_twiddles(nlon);
+    if (!rc && !ftw.empty()) rc = dalloc(&P->d_ftw, ftw.size() * sizeof(float));
     if (!rc) rc = dalloc(&P->d_lm, nc * sizeof(int2));
     if (!rc) rc = dalloc(&P->d_finc, nc * sizeof(double4_32a));
     if (!rc) rc = dalloc(&P->d_prepc, size_t(P->n_ext) * sizeof(double4_32a));
@@ -302,6 +309,7 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     up(P->d_rw, rw.data(), nlat * sizeof(double));
     up(P->d_tw, tw.data(), tw.size() * sizeof(double));
     up(P->d_tw32, tw32.data(), tw32.size() * sizeof(float));
+    if (!ftw.empty()) up(P->d_ftw, ftw.data(), ftw.size() * sizeof(float));
     up(P->d_lm, lm.data(), nc * sizeof(int2));
     up(P->d_finc, finc.data(), nc * sizeof(double4_32a));
     up(P->d_prepc, prepc.data(), size_t(P->n_ext) * sizeof(double4_32a));
@@ -468,7 +476,7 @@ int sphnse_stage_timing(sphnse_plan* P, int enable) {
             P->stage_n[s] = 0;
         }
     }
-    P->timing = enable != 0;
+    P->timing = unsigned(enable) & ((1u << SPHNSE_NSTAGES) - 1);
     return SPHNSE_OK;
 }
 
