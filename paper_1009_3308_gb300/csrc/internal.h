@@ -83,11 +83,13 @@ struct Tables {
 
 // tcgen05 path state (tensor maps and item schedules, built on first use)
 struct TcState {
-    void* map_hi = nullptr;      // CUtensorMap per (m, parity) block, global memory
+    void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
     void* map_lo = nullptr;
-    int4* ana_items = nullptr;
+    int4* ana_items = nullptr;   // (tile, first piece, piece count, MMA N)
     int* ana_off = nullptr;
+    int4* ana_pieces = nullptr;  // (m, parity, first tile row, end tile row)
     int ana_cta = 0;
+    int ana_nf = 0;
     bool ana_ready = false;
     void* smap_hi = nullptr;     // synthesis: tensor maps of the transposed tables
     void* smap_lo = nullptr;
@@ -95,6 +97,9 @@ struct TcState {
     void* tsyn_lo = nullptr;
     void* btiles = nullptr;      // synthesis B tiles [tile][16][64] bf16, swizzled (k_prep_tc)
     int* tile_off = nullptr;     // first tile of block (m, parity)
+    int2* syn_items = nullptr;   // (m, latitude tile) per CTA (LPT)
+    int* syn_off = nullptr;
+    int syn_cta = 0;
     size_t tsyn_bytes = 0;
     bool syn_ready = false;
 };

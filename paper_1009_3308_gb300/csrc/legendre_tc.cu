@@ -69,16 +69,27 @@ __device__ __forceinline__ uint32_t sw128_chunk(int r, int q) {
     return uint32_t(r) * 128u + (uint32_t(q ^ (r & 7)) << 4);
 }
 
+// Analysis items: tiles of 128 consecutive table rows (the (m, parity) blocks
+// packed back to back in degree order), each with up to 32 / (4 NF) pieces =
+// the blocks it overlaps.  Piece j owns B columns 4 NF j .. 4 NF j + 4 NF - 1
+// (hi parts, then lo parts) and the tile rows [s, e); the MMA computes all
+// columns for all rows and the epilogue keeps the columns of each row's piece.
 struct TcAnaArgs {
-    const CUtensorMap* map_hi;   // per (m, parity) block, global memory
+    const CUtensorMap* map_hi;   // whole table [n_ext][nh], box 64 x 128
     const CUtensorMap* map_lo;
-    const int4* items;           // (block, m, parity, row tile)
+    const int4* items;           // (tile, first piece, piece count, N)
     const int* item_off;         // per CTA
+    const int4* pieces;          // (m, parity, s, e)
     const float* gana;           // [NF][N+1][nlat] complex float (m-major)
     float* hana;                 // [n_ext][2 NF]
     unsigned* status;
-    int N, nh, nlat, nkt;
+    int N, nh, nlat, nkt, n_ext;
 };
+
+constexpr int TC_ANA_NS = 5;                   // A stages
+constexpr int TC_ANA_BROWS = 32;               // B rows (N) per item at most
+constexpr int TC_ANA_BTILE = TC_ANA_BROWS * TC_TILE_K * 2;   // 4 KB per K tile
+constexpr int TC_ANA_COLS = 128;               // TMEM: 2 buffers x 64 columns
 
 template <int NF>
 __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
@@ -86,13 +97,14 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
     // 1024-byte aligned base for the swizzled tiles
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    unsigned char* A_hi = smem;                                   // TC_NS x 16 KB
-    unsigned char* A_lo = A_hi + TC_NS * TC_ATILE;                // TC_NS x 16 KB
-    unsigned char* Bt = A_lo + TC_NS * TC_ATILE;                  // 2 bufs x nkt x 2 KB
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Bt + 2 * a.nkt * TC_BTILE);
+    constexpr int RP = 4 * NF;                                    // B rows per piece
+    unsigned char* A_hi = smem;                                   // NS x 16 KB
+    unsigned char* A_lo = A_hi + TC_ANA_NS * TC_ATILE;            // NS x 16 KB
+    unsigned char* Bt = A_lo + TC_ANA_NS * TC_ATILE;              // 2 bufs x nkt x 4 KB
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bt + 2 * a.nkt * TC_ANA_BTILE);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + TC_NS;
-    uint64_t* b_full = bars + 2 * TC_NS;
+    uint64_t* a_empty = bars + TC_ANA_NS;
+    uint64_t* b_full = bars + 2 * TC_ANA_NS;
     uint64_t* b_empty = b_full + 2;
     uint64_t* acc_full = b_full + 4;
     uint64_t* acc_empty = b_full + 6;
@@ -101,12 +113,12 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     const int N = a.N, nh = a.nh, nlat = a.nlat, nkt = a.nkt;
-    // rows 4 NF .. 15 of every B tile stay zero
-    for (int i = threadIdx.x; i < 2 * nkt * TC_BTILE / 16; i += blockDim.x)
+    // B rows past the pieces of an item are never read back; start them at zero
+    for (int i = threadIdx.x; i < 2 * nkt * TC_ANA_BTILE / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(Bt)[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async_smem();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_NS; ++s) {
+        for (int s = 0; s < TC_ANA_NS; ++s) {
             mbar_init(&a_full[s], 1);
             mbar_init(&a_empty[s], 1);
         }
@@ -120,7 +132,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, 64);
+        tmem_alloc(tmem_slot, TC_ANA_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -138,38 +150,40 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
                 for (int kt = 0; kt < nkt; ++kt, ++it) {
-                    const int s = it % TC_NS;
-                    if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status)) continue;
+                    const int s = it % TC_ANA_NS;
+                    if (it >= TC_ANA_NS && !mbar_wait(&a_empty[s], ((it / TC_ANA_NS) - 1) & 1, abort, a.status))
+                        continue;
                     if (*abort) continue;
                     mbar_arrive_expect_tx(&a_full[s], 2 * TC_ATILE);
-                    tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[itm.x], kt * TC_TILE_K, itm.w * TC_TILE_M, &a_full[s], pol);
-                    tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[itm.x], kt * TC_TILE_K, itm.w * TC_TILE_M, &a_full[s], pol);
+                    tma_load_2d(A_hi + s * TC_ATILE, a.map_hi, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
+                    tma_load_2d(A_lo + s * TC_ATILE, a.map_lo, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
                 }
             }
-            for (int k = it - TC_NS; k < it; ++k)
-                if (k >= 0) mbar_wait(&a_full[k % TC_NS], (k / TC_NS) & 1, abort, a.status);
+            for (int k = it - TC_ANA_NS; k < it; ++k)
+                if (k >= 0) mbar_wait(&a_full[k % TC_ANA_NS], (k / TC_ANA_NS) & 1, abort, a.status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(TC_TILE_M, TC_N);
             int it = 0;
             for (int i = 0; i < nI; ++i) {
+                const int4 itm = a.items[ib + i];
+                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w);
                 const int buf = i & 1, use = i >> 1;
                 bool ok = mbar_wait(&b_full[buf], use & 1, abort, a.status);
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status) && ok;
                 tc_fence_after();
-                const uint32_t d1 = tmem + uint32_t(buf * 2 * TC_N), d2 = d1 + TC_N;
+                const uint32_t d = tmem + uint32_t(buf * 64);
                 for (int kt = 0; kt < nkt; ++kt, ++it) {
-                    const int s = it % TC_NS;
-                    const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
+                    const int s = it % TC_ANA_NS;
+                    const bool okA = mbar_wait(&a_full[s], (it / TC_ANA_NS) & 1, abort, a.status);
                     tc_fence_after();
                     if (ok && okA && !*abort) {
-                        const unsigned char* bt = Bt + (buf * nkt + kt) * TC_BTILE;
+                        const unsigned char* bt = Bt + (buf * nkt + kt) * TC_ANA_BTILE;
 #pragma unroll
                         for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
                             const uint64_t bd = sdesc_sw128(bt + kk * 32);
-                            mma_bf16(d1, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
-                            mma_bf16(d2, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                         }
                     }
                     mma_commit(&a_empty[s]);
@@ -180,7 +194,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             if (nI > 0) mbar_wait(&acc_full[(nI - 1) & 1], ((nI - 1) >> 1) & 1, abort, a.status);
         }
     } else if (warp < 6) {
-        // B builders: task (K tile, chunk q of 8 latitudes, field f)
+        // B builders: task (piece, K tile, chunk q of 8 latitudes, field f)
         pdl_wait();
         const int ht = threadIdx.x - 64;
         const size_t ld = size_t(N + 1);
@@ -188,9 +202,12 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             const int buf = i & 1;
             if (i >= 2) mbar_wait(&b_empty[buf], ((i >> 1) - 1) & 1, abort, a.status);
             const int4 itm = a.items[ib + i];
-            const int m = itm.y, par = itm.z;
-            for (int task = ht; task < nkt * 8 * NF; task += 128) {
-                const int f = task % NF, q = (task / NF) & 7, kt = task / (8 * NF);
+            const int per_piece = nkt * 8 * NF;
+            for (int task = ht; task < itm.z * per_piece; task += 128) {
+                const int j = task / per_piece, tl = task % per_piece;
+                const int4 pc = a.pieces[itm.y + j];
+                const int m = pc.x, par = pc.y;
+                const int f = tl % NF, q = (tl / NF) & 7, kt = tl / (8 * NF);
                 const int p0 = kt * TC_TILE_K + q * 8;
                 const float* g = a.gana + (size_t(f) * ld + m) * size_t(nlat) * 2;
                 float nv[16], sv[16];
@@ -223,11 +240,12 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
                     re[e] = par ? nv[2 * e] - sr : nv[2 * e] + sr;
                     im[e] = par ? nv[2 * e + 1] - si : nv[2 * e + 1] + si;
                 }
-                unsigned char* tile = Bt + (buf * nkt + kt) * TC_BTILE;
-                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f, q)) = pack_hi(re);
-                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f + 1, q)) = pack_hi(im);
-                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * NF + 2 * f, q)) = pack_lo(re);
-                *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * NF + 2 * f + 1, q)) = pack_lo(im);
+                unsigned char* tile = Bt + (buf * nkt + kt) * TC_ANA_BTILE;
+                const int r0 = RP * j;
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(r0 + 2 * f, q)) = pack_hi(re);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(r0 + 2 * f + 1, q)) = pack_hi(im);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(r0 + 2 * NF + 2 * f, q)) = pack_lo(re);
+                *reinterpret_cast<uint4*>(tile + sw128_chunk(r0 + 2 * NF + 2 * f + 1, q)) = pack_lo(im);
             }
             fence_proxy_async_smem();
             mbar_arrive(&b_full[buf]);
@@ -236,33 +254,33 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
         // epilogue: TMEM lanes of this warp's quarter -> projection rows
         pdl_wait();
         const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;               // tile row of this lane
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
-            const int m = itm.y, par = itm.z, t = itm.w, buf = i & 1;
+            const int buf = i & 1;
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
-            float v1[16], v2[16];
-            const uint32_t ta = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * 2 * TC_N);
-            tmem_ld16(ta, v1);
-            tmem_ld16(ta + TC_N, v2);
+            const int row = itm.x * TC_TILE_M + r;
+            for (int j = 0; j < itm.z; ++j) {
+                const int4 pc = a.pieces[itm.y + j];
+                if (pc.w <= quarter * 32 || pc.z >= quarter * 32 + 32) continue;   // warp-uniform
+                float v[16];
+                tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * 64 + RP * j), v);
+                if (ok && r >= pc.z && r < pc.w && row < a.n_ext && !*abort) {
+#pragma unroll
+                    for (int c = 0; c < 2 * NF; ++c)
+                        a.hana[size_t(row) * 2 * NF + c] = v[c] + v[2 * NF + c];
+                }
+            }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
-            const int ne = ext_even(N, m), no = ext_odd(N, m);
-            const int nrows = par ? no : ne;
-            const int r = t * TC_TILE_M + quarter * 32 + lane;
-            if (ok && r < nrows && !*abort) {
-                const int row = ext_off(N, m) + (par ? ne : 0) + r;
-#pragma unroll
-                for (int c = 0; c < 2 * NF; ++c)
-                    a.hana[size_t(row) * 2 * NF + c] = (v1[c] + v1[2 * NF + c]) + (v2[c] + v2[2 * NF + c]);
-            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 64);
+        tmem_dealloc(tmem, TC_ANA_COLS);
     }
 }
 
@@ -279,29 +297,34 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
 struct TcSynArgs {
     const CUtensorMap* map_hi;   // per (m, parity) block of the transposed tables
     const CUtensorMap* map_lo;
-    const int* items;            // orders m per CTA (LPT)
+    const int2* items;           // (m, latitude tile) per CTA (LPT)
     const int* item_off;
     const unsigned char* btiles; // [tile][16][64] bf16, 128-byte swizzle (k_prep_tc)
     const int* tile_off;         // first tile of block b = 2 m + parity
     float* gsyn;                 // [3][N+1][nlat] complex (m-major)
     const double* sinth;
     unsigned* status;
-    int N, nh, nlat, nmt;
+    int N, nh, nlat;
 };
 
-constexpr int TC_SYN_COLS = 512;  // TMEM columns: 2 buffers x 2 parities x nmt (<= 4) x 2 x 16
+constexpr int TC_SYN_COLS = 64;   // TMEM columns: 2 buffers x 2 parities x 16
 constexpr int TC_SYN_STAGE = 2 * TC_ATILE + TC_BTILE;
 
-__host__ __device__ inline int syn_nkt(int N, int m, int par) {
+__host__ __device__ inline int syn_ndeg(int N, int m, int par) {
     const int n = par ? ext_odd(N, m) : ext_even(N, m);
-    return (((n + 7) / 8) * 8 + TC_TILE_K - 1) / TC_TILE_K;
+    return ((n + 7) / 8) * 8;
+}
+__host__ __device__ inline int syn_nkt(int N, int m, int par) {
+    return (syn_ndeg(N, m, par) + TC_TILE_K - 1) / TC_TILE_K;
 }
 
+// Item = (order m, latitude tile of 128 northern nodes): both parities into
+// their own accumulator (hi and lo table parts into the same one, as both
+// multiply the same B tile); K chunks of 16 degrees past the block are skipped.
 __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    const int nmt = a.nmt;
     unsigned char* A_hi = smem;
     unsigned char* A_lo = A_hi + TC_NS * TC_ATILE;
     unsigned char* Bs = A_lo + TC_NS * TC_ATILE;                 // TC_NS x 2 KB
@@ -344,21 +367,20 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const uint64_t polb = policy_evict_last();
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int m = a.items[ib + i];
+                const int2 itm = a.items[ib + i];
+                const int m = itm.x, mt = itm.y;
                 for (int par = 0; par < 2; ++par) {
                     const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
                     const unsigned char* bsrc = a.btiles + size_t(a.tile_off[b]) * TC_BTILE;
-                    for (int kt = 0; kt < nkt; ++kt)
-                        for (int mt = 0; mt < nmt; ++mt, ++it) {
-                            const int s = it % TC_NS;
-                            if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status))
-                                continue;
-                            if (*abort) continue;
-                            mbar_arrive_expect_tx(&a_full[s], TC_SYN_STAGE);
-                            tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                            tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                            bulk_g2s(Bs + s * TC_BTILE, bsrc + size_t(kt) * TC_BTILE, TC_BTILE, &a_full[s], polb);
-                        }
+                    for (int kt = 0; kt < nkt; ++kt, ++it) {
+                        const int s = it % TC_NS;
+                        if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status)) continue;
+                        if (*abort) continue;
+                        mbar_arrive_expect_tx(&a_full[s], TC_SYN_STAGE);
+                        tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        bulk_g2s(Bs + s * TC_BTILE, bsrc + size_t(kt) * TC_BTILE, TC_BTILE, &a_full[s], polb);
+                    }
                 }
             }
             for (int k = it - TC_NS; k < it; ++k)
@@ -369,30 +391,29 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             constexpr uint32_t idesc = idesc_bf16(TC_TILE_M, TC_N);
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int m = a.items[ib + i];
+                const int m = a.items[ib + i].x;
                 const int buf = i & 1, use = i >> 1;
                 bool ok = true;
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
-                    const int nkt = syn_nkt(N, m, par);
-                    for (int kt = 0; kt < nkt; ++kt)
-                        for (int mt = 0; mt < nmt; ++mt, ++it) {
-                            const int s = it % TC_NS;
-                            const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
-                            tc_fence_after();
-                            const uint32_t d = tmem + uint32_t(((buf * 2 + par) * nmt + mt) * 2 * TC_N);
-                            if (ok && okA && !*abort) {
-#pragma unroll
-                                for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
-                                    const uint64_t bd = sdesc_sw128(Bs + s * TC_BTILE + kk * 32);
-                                    mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
-                                    mma_bf16(d + TC_N, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc,
-                                             (kt | kk) != 0);
-                                }
+                    const int nkt = syn_nkt(N, m, par), nd = syn_ndeg(N, m, par);
+                    const uint32_t d = tmem + uint32_t((buf * 2 + par) * TC_N);
+                    for (int kt = 0; kt < nkt; ++kt, ++it) {
+                        const int s = it % TC_NS;
+                        const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
+                        tc_fence_after();
+                        // 16-degree chunks of this K tile that hold degrees of the block
+                        const int nkk = min(TC_TILE_K, nd - kt * TC_TILE_K + 15) / 16;
+                        if (ok && okA && !*abort) {
+                            for (int kk = 0; kk < nkk; ++kk) {
+                                const uint64_t bd = sdesc_sw128(Bs + s * TC_BTILE + kk * 32);
+                                mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                                mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                             }
-                            mma_commit(&a_empty[s]);
                         }
+                        mma_commit(&a_empty[s]);
+                    }
                 }
                 mma_commit(&acc_full[buf]);
             }
@@ -403,47 +424,42 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         const int quarter = warp & 3;
         const size_t ld = size_t(N + 1);
         for (int i = 0; i < nI; ++i) {
-            const int m = a.items[ib + i], buf = i & 1;
+            const int2 itm = a.items[ib + i];
+            const int m = itm.x, mt = itm.y, buf = i & 1;
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
             const float mm = float(m);
-            for (int mt = 0; mt < nmt; ++mt) {
-                float e1[16], e2[16], o1[16], o2[16];
-                const uint32_t lanes = uint32_t(quarter * 32) << 16;
-                const uint32_t ce = uint32_t(((buf * 2 + 0) * nmt + mt) * 2 * TC_N);
-                const uint32_t co = uint32_t(((buf * 2 + 1) * nmt + mt) * 2 * TC_N);
-                tmem_ld16(tmem + lanes + ce, e1);
-                tmem_ld16(tmem + lanes + ce + TC_N, e2);
-                tmem_ld16(tmem + lanes + co, o1);
-                tmem_ld16(tmem + lanes + co + TC_N, o2);
-                const int p = mt * TC_TILE_M + quarter * 32 + lane;
-                if (!ok || p >= nh || *abort) continue;
-                const float inv_s = float(1.0 / a.sinth[p]);
-                float E[6], O[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    E[c] = (e1[c] + e1[6 + c]) + (e2[c] + e2[6 + c]);
-                    O[c] = (o1[c] + o1[6 + c]) + (o2[c] + o2[6 + c]);
-                }
-#pragma unroll
-                for (int hemi = 0; hemi < 2; ++hemi) {
-                    const int row = hemi == 0 ? p : nlat - 1 - p;
-                    if (hemi == 1 && row == p) break;
-                    const float sg = hemi == 0 ? 1.f : -1.f;
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        const float gr = E[2 * f] + sg * O[2 * f];
-                        const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
-                        float2 o;
-                        if (f == 0) o = make_float2(gr, gi);
-                        else if (f == 1) o = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
-                        else o = make_float2(-gr * inv_s, -gi * inv_s);
-                        reinterpret_cast<float2*>(a.gsyn)[(size_t(f) * ld + m) * nlat + row] = o;
-                    }
-                }
-            }
+            float e[16], o[16];
+            const uint32_t lanes = uint32_t(quarter * 32) << 16;
+            tmem_ld16(tmem + lanes + uint32_t((buf * 2 + 0) * TC_N), e);
+            tmem_ld16(tmem + lanes + uint32_t((buf * 2 + 1) * TC_N), o);
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
+            const int p = mt * TC_TILE_M + quarter * 32 + lane;
+            if (!ok || p >= nh || *abort) continue;
+            const float inv_s = float(1.0 / a.sinth[p]);
+            float E[6], O[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                E[c] = e[c] + e[6 + c];
+                O[c] = o[c] + o[6 + c];
+            }
+#pragma unroll
+            for (int hemi = 0; hemi < 2; ++hemi) {
+                const int row = hemi == 0 ? p : nlat - 1 - p;
+                if (hemi == 1 && row == p) break;
+                const float sg = hemi == 0 ? 1.f : -1.f;
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const float gr = E[2 * f] + sg * O[2 * f];
+                    const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
+                    float2 ov;
+                    if (f == 0) ov = make_float2(gr, gi);
+                    else if (f == 1) ov = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
+                    else ov = make_float2(-gr * inv_s, -gi * inv_s);
+                    reinterpret_cast<float2*>(a.gsyn)[(size_t(f) * ld + m) * nlat + row] = ov;
+                }
+            }
         }
     }
     tc_fence_before();
@@ -523,41 +539,67 @@ static EncodeTiledFn encode_fn() {
 
 bool tc_supported(const sphnse_plan* P) { return P->nh % 8 == 0 && P->nh >= 64 && P->nlat % 2 == 0; }
 
-// Tensor maps over every (m, parity) block of the [ext row][nh] bf16 tables,
-// and the LPT schedule of (block, row tile) items over one CTA per SM.
-int tc_setup_analysis(sphnse_plan* P) {
-    if (P->tc.ana_ready) return SPHNSE_OK;
+// Tensor maps over the whole [ext row][nh] bf16 tables, the analysis items
+// (128-row tiles split into groups of at most 32 / (4 NF) overlapped blocks)
+// and their LPT schedule over one CTA per SM.
+int tc_setup_analysis(sphnse_plan* P, int nf) {
+    if (P->tc.ana_ready && P->tc.ana_nf == nf) return SPHNSE_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return SPHNSE_E_UNSUPPORTED;
+    auto& T = P->tc;
+    for (void* q : {T.map_hi, T.map_lo, static_cast<void*>(T.ana_items), static_cast<void*>(T.ana_off),
+                    static_cast<void*>(T.ana_pieces)})
+        if (q) cudaFree(q);
+    T.map_hi = T.map_lo = nullptr;
+    T.ana_items = nullptr;
+    T.ana_off = nullptr;
+    T.ana_pieces = nullptr;
+    T.ana_ready = false;
     const Tables& t = P->tab[SPHNSE_BF16X3];
-    const int N = P->N, nh = P->nh;
-    const int nblk = 2 * (N + 1);
-    std::vector<CUtensorMap> mh(nblk), ml(nblk);
-    std::vector<int4> items;
-    std::vector<int> cost;
-    for (int m = 0; m <= N; ++m) {
-        for (int par = 0; par < 2; ++par) {
-            const int ne = ext_even(N, m), no = ext_odd(N, m);
-            const int nrows = par ? no : ne;
-            const int r0 = ext_off(N, m) + (par ? ne : 0);
-            const int b = 2 * m + par;
-            const cuuint64_t dims[2] = {cuuint64_t(nh), cuuint64_t(nrows)};
-            const cuuint64_t strides[1] = {cuuint64_t(nh) * 2};
-            const cuuint32_t box[2] = {TC_TILE_K, TC_TILE_M};
-            const cuuint32_t es[2] = {1, 1};
-            for (int lo = 0; lo < 2; ++lo) {
-                const __nv_bfloat16* base = reinterpret_cast<const __nv_bfloat16*>(lo ? t.syn_lo : t.syn) +
-                                            size_t(r0) * nh;
-                CUresult r = enc(lo ? &ml[b] : &mh[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base),
-                                 dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
-            }
-            for (int tt = 0; tt * TC_TILE_M < nrows; ++tt) {
-                items.push_back(make_int4(b, m, par, tt));
-                cost.push_back(std::min(TC_TILE_M, nrows - tt * TC_TILE_M) + 16);
-            }
+    const int N = P->N, nh = P->nh, n_ext = P->n_ext;
+    CUtensorMap mh, ml;
+    {
+        const cuuint64_t dims[2] = {cuuint64_t(nh), cuuint64_t(n_ext)};
+        const cuuint64_t strides[1] = {cuuint64_t(nh) * 2};
+        const cuuint32_t box[2] = {TC_TILE_K, TC_TILE_M};
+        const cuuint32_t es[2] = {1, 1};
+        for (int lo = 0; lo < 2; ++lo) {
+            CUresult r = enc(lo ? &ml : &mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(lo ? t.syn_lo : t.syn),
+                             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
         }
+    }
+    // pieces of every tile: the blocks (m, parity) overlapping rows [128 T, 128 T + 128)
+    const int maxp = TC_ANA_BROWS / (4 * nf);
+    const int ntile = (n_ext + TC_TILE_M - 1) / TC_TILE_M;
+    std::vector<int4> pieces, items;
+    std::vector<int> cost;
+    {
+        std::vector<std::vector<int4>> per(ntile);
+        for (int m = 0; m <= N; ++m)
+            for (int par = 0; par < 2; ++par) {
+                const int ne = ext_even(N, m);
+                const int r0 = ext_off(N, m) + (par ? ne : 0), nr = par ? ext_odd(N, m) : ne;
+                for (int r = r0; r < r0 + nr;) {
+                    const int tt = r / TC_TILE_M, end = std::min(r0 + nr, (tt + 1) * TC_TILE_M);
+                    per[tt].push_back(make_int4(m, par, r - tt * TC_TILE_M, end - tt * TC_TILE_M));
+                    r = end;
+                }
+            }
+        for (int tt = 0; tt < ntile; ++tt)
+            for (size_t j0 = 0; j0 < per[tt].size(); j0 += maxp) {
+                const int np = int(std::min<size_t>(maxp, per[tt].size() - j0));
+                const int ncol = ((4 * nf * np + 15) / 16) * 16;
+                items.push_back(make_int4(tt, int(pieces.size()), np, ncol));
+                int rows = 0;
+                for (int j = 0; j < np; ++j) {
+                    pieces.push_back(per[tt][j0 + j]);
+                    rows += per[tt][j0 + j].w - per[tt][j0 + j].z;
+                }
+                cost.push_back(TC_TILE_M + 24 * np);
+                (void)rows;
+            }
     }
     // LPT: largest items first onto the least-loaded CTA
     std::vector<int> order(items.size());
@@ -577,17 +619,19 @@ int tc_setup_analysis(sphnse_plan* P) {
         flat.insert(flat.end(), bi.begin(), bi.end());
         off.push_back(int(flat.size()));
     }
-    auto& T = P->tc;
-    if (cudaMalloc(&T.map_hi, nblk * sizeof(CUtensorMap)) != cudaSuccess ||
-        cudaMalloc(&T.map_lo, nblk * sizeof(CUtensorMap)) != cudaSuccess ||
+    if (cudaMalloc(&T.map_hi, sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMalloc(&T.map_lo, sizeof(CUtensorMap)) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void**>(&T.ana_items), flat.size() * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&T.ana_off), off.size() * sizeof(int)) != cudaSuccess)
+        cudaMalloc(reinterpret_cast<void**>(&T.ana_off), off.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.ana_pieces), pieces.size() * sizeof(int4)) != cudaSuccess)
         return SPHNSE_E_NOMEM;
-    cudaMemcpy(T.map_hi, mh.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
-    cudaMemcpy(T.map_lo, ml.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.map_hi, &mh, sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.map_lo, &ml, sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     cudaMemcpy(T.ana_items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice);
     cudaMemcpy(T.ana_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.ana_pieces, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
     T.ana_cta = G;
+    T.ana_nf = nf;
     T.ana_ready = true;
     return check_cuda(cudaGetLastError());
 }
@@ -595,12 +639,13 @@ int tc_setup_analysis(sphnse_plan* P) {
 template <int NF>
 static int ana_tc_t(sphnse_plan* P) {
     const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
-    const size_t sm = 1024 + 2 * size_t(TC_NS) * TC_ATILE + 2 * size_t(nkt) * TC_BTILE + 256;
-    if (sm > 227 * 1024 || 4 * NF > TC_N) return SPHNSE_E_UNSUPPORTED;
+    const size_t sm = 1024 + 2 * size_t(TC_ANA_NS) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256;
+    if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_ana_tc<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    TcAnaArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi), reinterpret_cast<const CUtensorMap*>(P->tc.map_lo), P->tc.ana_items, P->tc.ana_off,
+    TcAnaArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi), reinterpret_cast<const CUtensorMap*>(P->tc.map_lo),
+                P->tc.ana_items, P->tc.ana_off, P->tc.ana_pieces,
                 reinterpret_cast<const float*>(P->d_gana), reinterpret_cast<float*>(P->d_hana), P->d_status,
-                P->N, P->nh, P->nlat, nkt};
+                P->N, P->nh, P->nlat, nkt, P->n_ext};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     const cudaError_t e = launch_pdl(k_ana_tc<NF>, dim3(P->tc.ana_cta), dim3(320), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
@@ -608,7 +653,7 @@ static int ana_tc_t(sphnse_plan* P) {
 }
 
 int launch_analysis_tc(sphnse_plan* P, int nfields) {
-    int rc = tc_setup_analysis(P);
+    int rc = tc_setup_analysis(P, nfields);
     if (rc) return rc;
     return nfields == 3 ? ana_tc_t<3>(P) : ana_tc_t<2>(P);
 }
@@ -680,6 +725,40 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemset(T.btiles, 0, size_t(toff[nblk]) * TC_BTILE);
     cudaMemcpy(T.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    // items (m, latitude tile), LPT on their stage counts (+1 for the epilogue)
+    {
+        const int nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
+        std::vector<int2> its;
+        std::vector<int> cost;
+        for (int m = 0; m <= N; ++m)
+            for (int mt = 0; mt < nmt; ++mt) {
+                its.push_back(make_int2(m, mt));
+                cost.push_back(syn_nkt(N, m, 0) + syn_nkt(N, m, 1) + 1);
+            }
+        std::vector<int> order(its.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        const int G = std::min<int>(P->n_cta, int(its.size()));
+        std::vector<std::vector<int2>> bins(G);
+        std::vector<long> load(G, 0);
+        for (int idx : order) {
+            const int bb = int(std::min_element(load.begin(), load.end()) - load.begin());
+            bins[bb].push_back(its[idx]);
+            load[bb] += cost[idx];
+        }
+        std::vector<int2> flat;
+        std::vector<int> offs(1, 0);
+        for (auto& bi : bins) {
+            flat.insert(flat.end(), bi.begin(), bi.end());
+            offs.push_back(int(flat.size()));
+        }
+        if (cudaMalloc(reinterpret_cast<void**>(&T.syn_items), flat.size() * sizeof(int2)) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&T.syn_off), offs.size() * sizeof(int)) != cudaSuccess)
+            return SPHNSE_E_NOMEM;
+        cudaMemcpy(T.syn_items, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        cudaMemcpy(T.syn_off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
+        T.syn_cta = G;
+    }
     T.tsyn_bytes = 2 * total * 2;
     T.syn_ready = true;
     return check_cuda(cudaGetLastError());
@@ -699,25 +778,23 @@ int launch_prep_tc(sphnse_plan* P, const double* alpha) {
 int launch_synthesis_tc(sphnse_plan* P) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
-    const int nmt = (P->nh + TC_TILE_M - 1) / TC_TILE_M;
-    if (nmt > 4) return SPHNSE_E_UNSUPPORTED;
     const size_t sm = 1024 + size_t(TC_NS) * TC_SYN_STAGE + 256;
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
-                reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->d_items, P->d_item_off,
+                reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->tc.syn_items, P->tc.syn_off,
                 static_cast<const unsigned char*>(P->tc.btiles), P->tc.tile_off, reinterpret_cast<float*>(P->d_gsyn),
-                P->d_s, P->d_status, P->N, P->nh, P->nlat, nmt};
+                P->d_s, P->d_status, P->N, P->nh, P->nlat};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->n_cta), dim3(192), sm, P->stream, a);
+    const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->tc.syn_cta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(e);
 }
 
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
-    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.smap_hi, T.smap_lo, T.tsyn_hi, T.tsyn_lo, T.btiles,
-                    T.tile_off};
+    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
+                    T.tsyn_lo, T.btiles, T.tile_off, T.syn_items, T.syn_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = TcState();
