@@ -97,6 +97,8 @@ struct TcState {
     void* tsyn_lo = nullptr;
     void* btiles = nullptr;      // synthesis B tiles [tile][16][64] bf16, swizzled (k_prep_tc)
     int* tile_off = nullptr;     // first tile of block (m, parity)
+    int2* tile_info = nullptr;   // (block, K tile) of every B tile, in tile order
+    int ntiles = 0;
     int2* syn_items = nullptr;   // (m, latitude tile) per CTA (LPT)
     int* syn_off = nullptr;
     int syn_cta = 0;

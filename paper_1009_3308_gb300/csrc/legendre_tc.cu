@@ -472,47 +472,53 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
 
 // Coefficient sets of the synthesis (zeta: lam^{1/2} a_K; theta: lam^{-1/2}
 // a_K; phi: c_down a_{K-1} + c_up a_{K+1}, the degree-shift form of
-// sin(theta) d/dtheta), written as the B tiles of k_syn_tc: thread (K tile
-// kt, chunk q, column c) of block b = (m, parity) computes column c for the 8
-// degrees K = m + par + 2 j, j = 64 kt + 8 q .. +7, and stores its hi part in
-// row c and its lo part in row 6 + c (rows 12-15 stay zero).
-__global__ void __launch_bounds__(384) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
-                                                 unsigned char* __restrict__ btiles, const int* __restrict__ tile_off,
-                                                 int N) {
+// sin(theta) d/dtheta), written as the B tiles of k_syn_tc.  Thread (tile,
+// chunk q) of the flat tile list computes the 8 degrees K = m + par + 2 j,
+// j = 64 kt + 8 q .. +7, of block b = (m, parity), and stores the hi parts of
+// the six columns in rows 0-5 and the lo parts in rows 6-11 (rows 12-15 stay
+// zero).  All of a thread's loads are independent, so they overlap.
+__global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
+                                                 unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
+                                                 int ntiles, int N) {
     pdl_launch();
-    const int b = blockIdx.x, m = b >> 1, par = b & 1;
+    const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
+    if (g >= ntiles) return;
+    const int2 ti = tinfo[g];
+    const int b = ti.x, kt = ti.y, m = b >> 1, par = b & 1;
     const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
-    const int kt = threadIdx.x >> 3, q = threadIdx.x & 7, c = threadIdx.y;
-    if (kt >= syn_nkt(N, m, par)) return;
     const int j0 = kt * TC_TILE_K + q * 8;
     const int lo = m > 0 ? m : 1;
     const int K0 = m + par + 2 * j0;
     const int pk = packed_off(N, m) - lo;   // packed index of degree K is pk + K
     const int r0 = ext_off(N, m) + (par ? ne : 0);
-    const bool shift = c >= 4;              // phi column: neighbours K - 1, K + 1
-    const bool im = c & 1;
-    float w[9];                             // alpha parts at K (8) or at K - 1 + 2 e (9)
+    float2 al[17];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-        const int K = shift ? K0 - 1 + 2 * e : K0 + 2 * e;
-        float v = 0.f;
-        if ((shift || e < 8) && K >= lo && K <= N) {
-            const double2 a = alpha[pk + K];
-            v = float(im ? a.y : a.x);
-        }
-        w[e] = v;
+    for (int e = 0; e < 17; ++e) {
+        const int K = K0 - 1 + e;
+        double2 v = make_double2(0.0, 0.0);
+        if (K >= lo && K <= N) v = alpha[pk + K];
+        al[e] = make_float2(float(v.x), float(v.y));
     }
-    float v[8];
+    float4 cf[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) cf[e] = (j0 + e < n) ? prepc[r0 + j0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float v[6][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int j = j0 + e;
-        float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < n) cf = prepc[r0 + j];
-        v[e] = c < 2 ? cf.x * w[e] : c < 4 ? cf.y * w[e] : fmaf(cf.z, w[e], cf.w * w[e + 1]);
+        const float2 am = al[2 * e], a0 = al[2 * e + 1], ap = al[2 * e + 2];
+        v[0][e] = cf[e].x * a0.x;
+        v[1][e] = cf[e].x * a0.y;
+        v[2][e] = cf[e].y * a0.x;
+        v[3][e] = cf[e].y * a0.y;
+        v[4][e] = fmaf(cf[e].z, am.x, cf[e].w * ap.x);
+        v[5][e] = fmaf(cf[e].z, am.y, cf[e].w * ap.y);
     }
-    unsigned char* tile = btiles + size_t(tile_off[b] + kt) * TC_BTILE;
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(c, q)) = pack_hi(v);
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(6 + c, q)) = pack_lo(v);
+    unsigned char* tile = btiles + size_t(g) * TC_BTILE;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(c, q)) = pack_hi(v[c]);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(6 + c, q)) = pack_lo(v[c]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -725,6 +731,15 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemset(T.btiles, 0, size_t(toff[nblk]) * TC_BTILE);
     cudaMemcpy(T.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    {   // flat tile list (block, K tile) for k_prep_tc
+        std::vector<int2> ti;
+        for (int b = 0; b < nblk; ++b)
+            for (int kt = 0; kt < toff[b + 1] - toff[b]; ++kt) ti.push_back(make_int2(b, kt));
+        if (cudaMalloc(reinterpret_cast<void**>(&T.tile_info), ti.size() * sizeof(int2)) != cudaSuccess)
+            return SPHNSE_E_NOMEM;
+        cudaMemcpy(T.tile_info, ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        T.ntiles = int(ti.size());
+    }
     // items (m, latitude tile), LPT on their stage counts (+1 for the epilogue)
     {
         const int nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
@@ -767,10 +782,10 @@ int tc_setup_synthesis(sphnse_plan* P) {
 int launch_prep_tc(sphnse_plan* P, const double* alpha) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
-    if (syn_nkt(P->N, 0, 0) * 8 > 64) return SPHNSE_E_UNSUPPORTED;
     stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep_tc<<<2 * (P->N + 1), dim3(64, 6), 0, P->stream>>>(reinterpret_cast<const double2*>(alpha), P->d_prepc32,
-                                                     static_cast<unsigned char*>(P->tc.btiles), P->tc.tile_off, P->N);
+    k_prep_tc<<<(P->tc.ntiles + 15) / 16, 128, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
+                                                               P->d_prepc32, static_cast<unsigned char*>(P->tc.btiles),
+                                                               P->tc.tile_info, P->tc.ntiles, P->N);
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
@@ -794,7 +809,7 @@ int launch_synthesis_tc(sphnse_plan* P) {
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
     void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
-                    T.tsyn_lo, T.btiles, T.tile_off, T.syn_items, T.syn_off};
+                    T.tsyn_lo, T.btiles, T.tile_off, T.syn_items, T.syn_off, T.tile_info};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = TcState();
