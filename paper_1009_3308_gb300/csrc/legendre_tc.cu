@@ -304,7 +304,7 @@ struct TcSynArgs {
     float* gsyn;                 // [3][N+1][nlat] complex (m-major)
     const double* sinth;
     unsigned* status;
-    int N, nh, nlat;
+    int N, nh, nlat, nblk;
 };
 
 constexpr int TC_SYN_COLS = 64;   // TMEM columns: 2 buffers x 2 parities x 16
@@ -316,6 +316,11 @@ __host__ __device__ inline int syn_ndeg(int N, int m, int par) {
 }
 __host__ __device__ inline int syn_nkt(int N, int m, int par) {
     return (syn_ndeg(N, m, par) + TC_TILE_K - 1) / TC_TILE_K;
+}
+// width of the last K tile of a block, rounded up to the 16-degree MMA chunk
+__host__ __device__ inline int syn_tailw(int N, int m, int par) {
+    const int rem = syn_ndeg(N, m, par) - (syn_nkt(N, m, par) - 1) * TC_TILE_K;
+    return ((rem + 15) / 16) * 16;
 }
 
 // Item = (order m, latitude tile of 128 northern nodes): both parities into
@@ -371,14 +376,18 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 const int m = itm.x, mt = itm.y;
                 for (int par = 0; par < 2; ++par) {
                     const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
+                    const int tw = syn_tailw(N, m, par);
                     const unsigned char* bsrc = a.btiles + size_t(a.tile_off[b]) * TC_BTILE;
                     for (int kt = 0; kt < nkt; ++kt, ++it) {
                         const int s = it % TC_NS;
                         if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status)) continue;
                         if (*abort) continue;
-                        mbar_arrive_expect_tx(&a_full[s], TC_SYN_STAGE);
-                        tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                        tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[b], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        const bool last = kt == nkt - 1;
+                        const int w = last ? tw : TC_TILE_K;
+                        const int mi = last ? a.nblk + b : b;
+                        mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2 + TC_BTILE));
+                        tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
                         bulk_g2s(Bs + s * TC_BTILE, bsrc + size_t(kt) * TC_BTILE, TC_BTILE, &a_full[s], polb);
                     }
                 }
@@ -701,28 +710,34 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemcpy(T.tsyn_hi, hi.data(), total * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(T.tsyn_lo, lo.data(), total * 2, cudaMemcpyHostToDevice);
-    std::vector<CUtensorMap> mh(nblk), ml(nblk);
+    // per block two maps: box 64 for full K tiles (entries [0, nblk)) and box
+    // syn_tailw for the last K tile (entries [nblk, 2 nblk)); a narrower box
+    // keeps the 128-byte row pitch of the swizzled tile, so the MMA
+    // descriptors are the same and only the 16-degree chunks it fills are read
+    std::vector<CUtensorMap> mh(2 * nblk), ml(2 * nblk);
     for (int b = 0; b < nblk; ++b) {
         const int m = b / 2, par = b % 2;
-        const int n = par ? ext_odd(N, m) : ext_even(N, m);
-        const int np = ((n + 7) / 8) * 8;
+        const int np = syn_ndeg(N, m, par);
         const cuuint64_t dims[2] = {cuuint64_t(np), cuuint64_t(nh)};
         const cuuint64_t strides[1] = {cuuint64_t(np) * 2};
-        const cuuint32_t box[2] = {TC_TILE_K, TC_TILE_M};
         const cuuint32_t es[2] = {1, 1};
-        for (int l = 0; l < 2; ++l) {
-            __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(l ? T.tsyn_lo : T.tsyn_hi) + off[b];
-            CUresult r = enc(l ? &ml[b] : &mh[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
+        for (int tail = 0; tail < 2; ++tail) {
+            const cuuint32_t box[2] = {cuuint32_t(tail ? syn_tailw(N, m, par) : TC_TILE_K), TC_TILE_M};
+            for (int l = 0; l < 2; ++l) {
+                __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(l ? T.tsyn_lo : T.tsyn_hi) + off[b];
+                CUresult r = enc(l ? &ml[tail * nblk + b] : &mh[tail * nblk + b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                 base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
+            }
         }
     }
-    if (cudaMalloc(&T.smap_hi, nblk * sizeof(CUtensorMap)) != cudaSuccess ||
-        cudaMalloc(&T.smap_lo, nblk * sizeof(CUtensorMap)) != cudaSuccess)
+    if (cudaMalloc(&T.smap_hi, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMalloc(&T.smap_lo, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess)
         return SPHNSE_E_NOMEM;
-    cudaMemcpy(T.smap_hi, mh.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
-    cudaMemcpy(T.smap_lo, ml.data(), nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.smap_hi, mh.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.smap_lo, ml.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     // B tiles of the coefficient sets (k_prep_tc): one 2 KB tile per (m, parity, K tile)
     std::vector<int> toff(nblk + 1, 0);
     for (int b = 0; b < nblk; ++b) toff[b + 1] = toff[b] + syn_nkt(N, b / 2, b % 2);
@@ -799,7 +814,7 @@ int launch_synthesis_tc(sphnse_plan* P) {
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->tc.syn_items, P->tc.syn_off,
                 static_cast<const unsigned char*>(P->tc.btiles), P->tc.tile_off, reinterpret_cast<float*>(P->d_gsyn),
-                P->d_s, P->d_status, P->N, P->nh, P->nlat};
+                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1)};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->tc.syn_cta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
