@@ -247,10 +247,10 @@ int batched_rhs(sphnse_ensemble* E, const double2* x, double2* F) {
         const double* xb = reinterpret_cast<const double*>(x + B.off);
         double* Fb = reinterpret_cast<double*>(F + B.off);
         if ((rc = launch_prep32_batch(P, B.nb, xb, B.bsyn, B.sb))) return rc;
-        if ((rc = launch_synthesis_stream_batch(P, B.items, B.item_off, B.ncta, B.bsyn, B.sb, B.gsyn, B.sg)))
+        if ((rc = launch_synthesis_stream_batch(P, B.items, B.item_off, B.ncta, B.bsyn, B.sb, B.gsyn, B.sg, 0)))
             return rc;
         if (ring4_ok(P)) {
-            if ((rc = launch_ring4(P, B.nb, B.gsyn, B.sg, B.gana, B.sa))) return rc;
+            if ((rc = launch_ring4(P, B.nb, B.gsyn, B.sg, B.gana, B.sa, 0))) return rc;
         } else {
             if ((rc = launch_transpose(P, B.gsyn, B.gsyn_r, P->N + 1, P->nlat, 3 * B.nb, SPHNSE_FP32))) return rc;
             if ((rc = launch_ring_batch(P, B.nb, B.gsyn_r, B.sg, B.gana_r, B.sa))) return rc;

@@ -39,6 +39,14 @@ __host__ __device__ inline void packed_lm(int N, int i, int& L, int& m) {
     L = ip - off(u) + m;
 }
 
+// Complex index of (field f, order m, latitude row) in a synthesis output:
+// order-major [f][m][row], or latitude-pair-major [f][row / 2][m][row % 2]
+// (pairs != 0), the layout the four-step ring kernel reads contiguously.
+__host__ __device__ inline size_t gsyn_index(int pairs, int f, int m, int row, int N, int nlat) {
+    return pairs ? ((size_t(f) * (nlat / 2) + row / 2) * size_t(N + 1) + m) * 2 + (row & 1)
+                 : (size_t(f) * (N + 1) + m) * size_t(nlat) + row;
+}
+
 // Extended-degree ("ext") rows: for each m the degrees K = m..N+1 (n_m = N+2-m
 // of them), split by the parity of K - m: even rows first (K = m + 2j,
 // j < ne(m)), then odd rows (K = m + 1 + 2j, j < no(m)).  Degree N+1 is needed
@@ -175,7 +183,8 @@ enum RingMode { RING_RHS = 0, RING_GRID = 1, RING_PROJECT = 2, RING_ADJOINT = 3 
 // prep: coefficient sets for synthesis.  nsets fields from alpha (3: zeta,
 // theta, phi) and optionally 2 more (theta, phi) from beta scaled by 1/s_m.
 int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int prec);
-int launch_synthesis(sphnse_plan* P, int nfields, int prec);
+// pairs != 0: write the latitude-pair-major layout of gsyn_index
+int launch_synthesis(sphnse_plan* P, int nfields, int prec, int pairs = 0);
 int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const double* gin1,
                 double* gout0, double* gout1, double* gout2);
 int launch_analysis(sphnse_plan* P, int nfields, int prec);
@@ -188,21 +197,21 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha,
 
 int ensure_tables(sphnse_plan* P, int prec);
 bool stream_ok(const sphnse_plan* P, int prec);
-int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec);
+int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec, int pairs = 0);
 bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
-int launch_synthesis_tc(sphnse_plan* P);
+int launch_synthesis_tc(sphnse_plan* P, int pairs);
 int launch_prep_tc(sphnse_plan* P, const double* alpha);
 // batched FP32 passes over instances of one truncation (ensemble)
 int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride);
 int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
-                                  const float* bsyn, size_t sb, float* gsyn, size_t sg);
+                                  const float* bsyn, size_t sb, float* gsyn, size_t sg, int pairs);
 int launch_ring_batch(sphnse_plan* P, int nb, const float* gsyn_r, size_t sgs, float* gana_r, size_t sga);
 // four-step FP32 RHS ring kernel on the order-major buffers (M = 24 M2, M2 = 4..64, nlat even)
 int ring4_m2(int nlon, int nlat);
 bool ring4_ok(const sphnse_plan* P);
 std::vector<float> ring4_twiddles(int nlon);
-int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga);
+int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga, int pairs);
 int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
                                  const float* gana, size_t sa, float* hana, size_t sh);
 int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstride, const double* alpha,

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128) k_prep32(const double2* __restrict__ alph
 template <typename T, int NF>
 __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, const T* __restrict__ bsyn,
                                                     T* __restrict__ gsyn, const double* __restrict__ sinth,
-                                                    int N, int nh, int nlat) {
+                                                    int N, int nh, int nlat, int pairs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* B = reinterpret_cast<T*>(smem_raw);
     const int m = blockIdx.y;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, c
                 outr = -gr * inv_s;
                 outi = -gi * inv_s;
             }
-            T* dst = gsyn + ((size_t(f) * ld + m) * nlat + row) * 2;
+            T* dst = gsyn + gsyn_index(pairs, f, m, row, N, nlat) * 2;
             dst[0] = outr;
             dst[1] = outi;
         }
@@ -356,7 +356,7 @@ int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int pre
 }
 
 template <typename T, int NF>
-static int synth_t(sphnse_plan* P) {
+static int synth_t(sphnse_plan* P, int pairs) {
     dim3 blk(128), grd((P->nh + 127) / 128, P->N + 1);
     size_t sm = size_t(P->N + 2) * 2 * NF * sizeof(T);
     if (sm > 48 * 1024)
@@ -364,18 +364,18 @@ static int synth_t(sphnse_plan* P) {
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     k_synthesis<T, NF><<<grd, blk, sm, P->stream>>>(
         reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
-        reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn), P->d_s, P->N, P->nh, P->nlat);
+        reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn), P->d_s, P->N, P->nh, P->nlat, pairs);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(cudaGetLastError());
 }
 
-int launch_synthesis(sphnse_plan* P, int nfields, int prec) {
+int launch_synthesis(sphnse_plan* P, int nfields, int prec, int pairs) {
     if (stream_ok(P, prec)) {
-        int rc = launch_synthesis_stream(P, nfields, prec);
+        int rc = launch_synthesis_stream(P, nfields, prec, pairs);
         if (rc != SPHNSE_E_UNSUPPORTED) return rc;
     }
-    if (prec == SPHNSE_FP64) return nfields == 5 ? synth_t<double, 5>(P) : synth_t<double, 3>(P);
-    return nfields == 5 ? synth_t<float, 5>(P) : synth_t<float, 3>(P);
+    if (prec == SPHNSE_FP64) return nfields == 5 ? synth_t<double, 5>(P, pairs) : synth_t<double, 3>(P, pairs);
+    return nfields == 5 ? synth_t<float, 5>(P, pairs) : synth_t<float, 3>(P, pairs);
 }
 
 template <typename T, int NF>

@@ -56,6 +56,7 @@ struct StreamArgs {
     // batches: an item v stands for instance v / (N+1) and order v % (N+1);
     // per-instance strides (elements) of bsyn, gsyn, gana, hana
     size_t sb, sg, sa, sh;
+    int pairs;           // gsyn layout (gsyn_index)
 };
 
 // chunk c of order m: rows [c HR, c HR + HR) of the even and of the odd block
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(512, 1) k_syn_stream(StreamArgs a) {
                         if (f == 0) { o0 = gr; o1 = gi; }
                         else if (f == 1 || f == 3) { o0 = -mm * gi * inv_s; o1 = mm * gr * inv_s; }
                         else { o0 = -gr * inv_s; o1 = -gi * inv_s; }
-                        T* d = gdst + ((size_t(f) * (N + 1) + m) * nlat + row) * 2;
+                        T* d = gdst + gsyn_index(a.pairs, f, m, row, N, nlat) * 2;
                         d[0] = o0;
                         d[1] = o1;
                     }
@@ -371,7 +372,7 @@ bool stream_ok(const sphnse_plan* P, int prec) {
 }
 
 template <typename T, int NF>
-static int syn_stream_t(sphnse_plan* P) {
+static int syn_stream_t(sphnse_plan* P, int pairs) {
     constexpr int HR = half_rows<T>();
     constexpr int V = Vec<T>::n;
     const int tpg = ((P->nh / V + 31) / 32) * 32;
@@ -383,7 +384,7 @@ static int syn_stream_t(sphnse_plan* P) {
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_syn_stream<T, NF, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, P->d_bsyn, P->d_gsyn, nullptr, nullptr,
-                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
+                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0, pairs};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     launch_pdl(k_syn_stream<T, NF, HR>, dim3(P->n_cta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
@@ -401,16 +402,17 @@ static int ana_stream_t(sphnse_plan* P) {
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_ana_stream<T, NF, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, nullptr, nullptr, P->d_gana, P->d_hana,
-                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0};
+                 P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     launch_pdl(k_ana_stream<T, NF, HR, NTEAM>, dim3(P->n_cta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
     return check_cuda(cudaGetLastError());
 }
 
-int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec) {
-    if (prec == SPHNSE_FP64) return nfields == 5 ? syn_stream_t<double, 5>(P) : syn_stream_t<double, 3>(P);
-    return nfields == 5 ? syn_stream_t<float, 5>(P) : syn_stream_t<float, 3>(P);
+int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec, int pairs) {
+    if (prec == SPHNSE_FP64)
+        return nfields == 5 ? syn_stream_t<double, 5>(P, pairs) : syn_stream_t<double, 3>(P, pairs);
+    return nfields == 5 ? syn_stream_t<float, 5>(P, pairs) : syn_stream_t<float, 3>(P, pairs);
 }
 
 int launch_analysis_stream(sphnse_plan* P, int nfields, int prec) {
@@ -420,7 +422,7 @@ int launch_analysis_stream(sphnse_plan* P, int nfields, int prec) {
 
 // FP32 batched streaming passes over instances (items = inst * (N+1) + m)
 int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,
-                                  const float* bsyn, size_t sb, float* gsyn, size_t sg) {
+                                  const float* bsyn, size_t sb, float* gsyn, size_t sg, int pairs) {
     constexpr int HR = half_rows<float>();
     constexpr int NST = nst<float>();
     const int tpg = ((P->nh / 4 + 31) / 32) * 32;
@@ -430,7 +432,7 @@ int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* i
     if (threads > 512 || sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_syn_stream<float, 3, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[SPHNSE_FP32].syn, bsyn, gsyn, nullptr, nullptr, P->d_s, items, item_off, P->d_status,
-                 P->N, P->nh, P->nlat, sb, sg, 0, 0};
+                 P->N, P->nh, P->nlat, sb, sg, 0, 0, pairs};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     launch_pdl(k_syn_stream<float, 3, HR>, dim3(ncta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
@@ -448,7 +450,7 @@ int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* it
     if (sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(k_ana_stream<float, 2, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     StreamArgs a{P->tab[SPHNSE_FP32].syn, nullptr, nullptr, gana, hana, P->d_s, items, item_off, P->d_status,
-                 P->N, P->nh, P->nlat, 0, 0, sa, sh};
+                 P->N, P->nh, P->nlat, 0, 0, sa, sh, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     launch_pdl(k_ana_stream<float, 2, HR, NTEAM>, dim3(ncta), dim3(threads), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);

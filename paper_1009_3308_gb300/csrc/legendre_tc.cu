@@ -304,7 +304,7 @@ struct TcSynArgs {
     float* gsyn;                 // [3][N+1][nlat] complex (m-major)
     const double* sinth;
     unsigned* status;
-    int N, nh, nlat, nblk;
+    int N, nh, nlat, nblk, pairs;
 };
 
 constexpr int TC_SYN_COLS = 64;   // TMEM columns: 2 buffers x 2 parities x 16
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                     if (f == 0) ov = make_float2(gr, gi);
                     else if (f == 1) ov = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
                     else ov = make_float2(-gr * inv_s, -gi * inv_s);
-                    reinterpret_cast<float2*>(a.gsyn)[(size_t(f) * ld + m) * nlat + row] = ov;
+                    reinterpret_cast<float2*>(a.gsyn)[gsyn_index(a.pairs, f, m, row, N, nlat)] = ov;
                 }
             }
         }
@@ -805,7 +805,7 @@ int launch_prep_tc(sphnse_plan* P, const double* alpha) {
     return check_cuda(cudaGetLastError());
 }
 
-int launch_synthesis_tc(sphnse_plan* P) {
+int launch_synthesis_tc(sphnse_plan* P, int pairs) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
     const size_t sm = 1024 + size_t(TC_NS) * TC_SYN_STAGE + 256;
@@ -814,7 +814,7 @@ int launch_synthesis_tc(sphnse_plan* P) {
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->tc.syn_items, P->tc.syn_off,
                 static_cast<const unsigned char*>(P->tc.btiles), P->tc.tile_off, reinterpret_cast<float*>(P->d_gsyn),
-                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1)};
+                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->tc.syn_cta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);

@@ -120,10 +120,16 @@ int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, doubl
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
     int rc;
     const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
+    const bool ring4 = prec == SPHNSE_FP32 && ring4_ok(P);
+    // the tensor-core synthesis writes the latitude-pair-major layout the
+    // four-step ring kernel reads contiguously (its epilogue warps are off the
+    // streaming path); the FP32 streaming synthesis keeps the order-major one
+    const int pairs = ring4 && tc;
     if ((rc = tc ? launch_prep_tc(P, alpha) : launch_prep(P, alpha, nullptr, prec))) return rc;
-    if ((rc = tc ? launch_synthesis_tc(P) : launch_synthesis(P, 3, prec))) return rc;
-    if (prec == SPHNSE_FP32 && ring4_ok(P)) {
-        if ((rc = launch_ring4(P, 1, static_cast<const float*>(P->d_gsyn), 0, static_cast<float*>(P->d_gana), 0)))
+    if ((rc = tc ? launch_synthesis_tc(P, pairs) : launch_synthesis(P, 3, prec))) return rc;
+    if (ring4) {
+        if ((rc = launch_ring4(P, 1, static_cast<const float*>(P->d_gsyn), 0, static_cast<float*>(P->d_gana), 0,
+                               pairs)))
             return rc;
     } else {
         if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;

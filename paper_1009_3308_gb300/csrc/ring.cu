@@ -356,7 +356,8 @@ int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const do
 
 // ---------------------------------------------------------------------------
 // Four-step ring kernel for M = 24 M2 (M2 = 4 .. 64), FP32, RHS mode, reading
-// and writing the order-major spectra of the Legendre kernels directly.
+// the synthesis output (order-major or latitude-pair-major) and writing the
+// order-major spectra of the analysis directly, without transposes.
 //
 // With n = t + M2 n1 and k = k1 + 24 k2 (t, k2 < M2; n1, k1 < 24), and
 // t = b + B a', k2 = c + A d (M2 = A B):
@@ -435,10 +436,11 @@ struct Ring4Args {
     float two_omega;
     const double* x;       // cos(theta)
     const double* rw;      // (2 pi / M) w_p / sin(theta_p)
-    const float2* gsyn;    // [3][N+1][nlat] complex (order-major)
+    const float2* gsyn;    // three complex spectra, layout gsyn_index(pairs, ...)
     float2* gana;          // [2][N+1][nlat] complex (order-major)
     const float2* ftw;     // tw1 [24][P1] = e^{+2 pi i t k1 / M}, then tw2 [A][B+1] = e^{+2 pi i b c / M2}
     size_t sgs, sga;       // per-instance strides (complex entries) along gridDim.y
+    int pairs;             // input layout: latitude-pair-major (1) or order-major (0)
 };
 
 template <int M2>
@@ -451,7 +453,22 @@ __global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
     float2* tw1 = sm4;
     float2* tw2 = tw1 + 24 * P1;
     float2* buf = tw2 + ((A * B2 + 1) & ~1);
-    for (int i = threadIdx.x; i < 24 * P1 + A * B2; i += 128) tw1[i] = a.ftw[i];
+    // twiddles do not depend on the predecessor: stage them before waiting for it,
+    // with all of a thread's loads issued before its stores
+    constexpr int NTW = (24 * P1 + A * B2 + 127) / 128;
+    {
+        float2 tv[NTW];
+#pragma unroll
+        for (int k = 0; k < NTW; ++k) {
+            const int i = threadIdx.x + 128 * k;
+            tv[k] = i < 24 * P1 + A * B2 ? __ldg(a.ftw + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < NTW; ++k) {
+            const int i = threadIdx.x + 128 * k;
+            if (i < 24 * P1 + A * B2) tw1[i] = tv[k];
+        }
+    }
     pdl_launch();
     pdl_wait();
     const int N = a.N, nlat = a.nlat, ld = N + 1;
@@ -460,17 +477,20 @@ __global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
     float2* ga = a.gana + size_t(blockIdx.y) * a.sga;
 
     // stage the spectra: ring r, field f, order m -> buf[r RING + f (N+1) + m].
-    // 3 (N+1) G / 2 <= 3 (8 M2) (64 / M2) = 1536 float4 loads per CTA: all of a
-    // thread's loads are issued before the first store, so their L2 latencies overlap.
+    // In the latitude-pair-major input, [f][row / 2][m][row % 2], the CTA's
+    // pairs are contiguous runs of (N+1) float4 per field; the order-major
+    // input gives one float4 per (f, m).  3 (N+1) G / 2 <= 1536 float4 loads
+    // per CTA, all of a thread's issued before its stores.
     constexpr int NLD = (3 * 8 * M2 * GP + 127) / 128;
     float4 stv[NLD];
 #pragma unroll
     for (int k = 0; k < NLD; ++k) {
         const int i = threadIdx.x + 128 * k;
-        const int rp = i % GP, fm = i / GP;
-        const int l = lat0 + 2 * rp;
+        const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
+        const int pr = lat0 / 2 + rp;
         stv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < 3 * ld * GP && l < nlat) stv[k] = __ldcs(reinterpret_cast<const float4*>(gs + size_t(fm) * nlat + l));
+        if (i < 3 * ld * GP && 2 * pr < nlat)
+            stv[k] = __ldcs(reinterpret_cast<const float4*>(gs + gsyn_index(a.pairs, f, m, 2 * pr, N, nlat)));
     }
     const int r = threadIdx.x / M2, t = threadIdx.x % M2;
     const int lat = lat0 + r;
@@ -481,9 +501,9 @@ __global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
     for (int k = 0; k < NLD; ++k) {
         const int i = threadIdx.x + 128 * k;
         if (i < 3 * ld * GP) {
-            const int rp = i % GP, fm = i / GP;
-            buf[(2 * rp) * RING + fm] = make_float2(stv[k].x, stv[k].y);
-            buf[(2 * rp + 1) * RING + fm] = make_float2(stv[k].z, stv[k].w);
+            const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
+            buf[(2 * rp) * RING + f * ld + m] = make_float2(stv[k].x, stv[k].y);
+            buf[(2 * rp + 1) * RING + f * ld + m] = make_float2(stv[k].z, stv[k].w);
         }
     }
     __syncthreads();
@@ -664,7 +684,7 @@ static constexpr size_t ring4_smem() {
 }
 
 template <int M2>
-static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga) {
+static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga, int pairs) {
     constexpr size_t sm = ring4_smem<M2>();
     static_assert(sm <= 227 * 1024, "ring4 shared memory");
     cudaFuncSetAttribute(k_ring4<M2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -679,6 +699,7 @@ static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float*
     a.ftw = reinterpret_cast<const float2*>(P->d_ftw);
     a.sgs = sgs / 2;
     a.sga = sga / 2;
+    a.pairs = pairs;
     constexpr int G = 128 / M2;
     return check_cuda(launch_pdl(k_ring4<M2>, dim3((P->nlat + G - 1) / G, nb), dim3(128), sm, P->stream, a));
 }
@@ -722,15 +743,15 @@ std::vector<float> ring4_twiddles(int nlon) {
 }
 
 // FP32 RHS ring pass over nb instances, order-major buffers
-int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga) {
+int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga, int pairs) {
     stage_begin(P, SPHNSE_STAGE_RING);
     int rc;
     switch (ring4_m2(P->nlon, P->nlat)) {
-        case 64: rc = ring4_t<64>(P, nb, gsyn, sgs, gana, sga); break;
-        case 32: rc = ring4_t<32>(P, nb, gsyn, sgs, gana, sga); break;
-        case 16: rc = ring4_t<16>(P, nb, gsyn, sgs, gana, sga); break;
-        case 8: rc = ring4_t<8>(P, nb, gsyn, sgs, gana, sga); break;
-        case 4: rc = ring4_t<4>(P, nb, gsyn, sgs, gana, sga); break;
+        case 64: rc = ring4_t<64>(P, nb, gsyn, sgs, gana, sga, pairs); break;
+        case 32: rc = ring4_t<32>(P, nb, gsyn, sgs, gana, sga, pairs); break;
+        case 16: rc = ring4_t<16>(P, nb, gsyn, sgs, gana, sga, pairs); break;
+        case 8: rc = ring4_t<8>(P, nb, gsyn, sgs, gana, sga, pairs); break;
+        case 4: rc = ring4_t<4>(P, nb, gsyn, sgs, gana, sga, pairs); break;
         default: rc = SPHNSE_E_UNSUPPORTED;
     }
     stage_end(P, SPHNSE_STAGE_RING);
