@@ -200,7 +200,7 @@ class Integrator:
 class Ensemble:
     """Batched ensemble of independent problems (sphnse_ensemble)."""
 
-    def __init__(self, Ls, nus, Omega, device=None):
+    def __init__(self, Ls, nus, Omega, device=None, precision="fp32"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libsphnse runs on a CUDA device; none is available")
@@ -216,6 +216,13 @@ class Ensemble:
         self._h = ctypes.c_void_p(h)
         self.n = n
         self.Ls = list(Ls)
+        if precision != "fp32":
+            self.set_precision(precision)
+
+    def set_precision(self, precision):
+        """"fp32" (streaming FP32 contractions) or "bf16x3" (the instances of
+        each truncation share every table tile of a tensor-core synthesis)."""
+        self.set("PRECISION", PRECISION[precision])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -204,6 +204,8 @@ struct Bucket {
     int* item_off = nullptr;
     int ncta = 0;
     double* nu_dev = nullptr;
+    TcBatch tcb;               // BF16X3: instance groups of the tensor-core synthesis
+    bool tc = false;
 };
 
 }  // namespace
@@ -216,6 +218,7 @@ struct sphnse_ensemble {
     double Omega = 0;
     double rtol = 1e-6, atol = 1e-12, h_max = 1.0;
     int max_order = 5, newton_max = 4;
+    int precision = SPHNSE_FP32;     // FP32 streaming, or BF16X3 tensor-core synthesis (batched)
     cudaStream_t stream = nullptr;   // the ensemble's own stream: all work, capture and replay
     cudaStream_t user = nullptr;     // the caller's stream, joined by events at API boundaries
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -246,9 +249,15 @@ int batched_rhs(sphnse_ensemble* E, const double2* x, double2* F) {
         P->stream = E->stream;
         const double* xb = reinterpret_cast<const double*>(x + B.off);
         double* Fb = reinterpret_cast<double*>(F + B.off);
-        if ((rc = launch_prep32_batch(P, B.nb, xb, B.bsyn, B.sb))) return rc;
-        if ((rc = launch_synthesis_stream_batch(P, B.items, B.item_off, B.ncta, B.bsyn, B.sb, B.gsyn, B.sg, 0)))
-            return rc;
+        if (B.tc) {
+            // all instances of the bucket share every table tile of the synthesis
+            if ((rc = launch_prep_tc_batch(P, B.tcb, xb))) return rc;
+            if ((rc = launch_synthesis_tc_batch(P, B.tcb, B.gsyn, B.sg, 0))) return rc;
+        } else {
+            if ((rc = launch_prep32_batch(P, B.nb, xb, B.bsyn, B.sb))) return rc;
+            if ((rc = launch_synthesis_stream_batch(P, B.items, B.item_off, B.ncta, B.bsyn, B.sb, B.gsyn, B.sg, 0)))
+                return rc;
+        }
         if (ring4_ok(P)) {
             if ((rc = launch_ring4(P, B.nb, B.gsyn, B.sg, B.gana, B.sa, 0))) return rc;
         } else {
@@ -313,6 +322,7 @@ void destroy_ens(sphnse_ensemble* E) {
         void* ptrs[] = {B.bsyn, B.gsyn, B.gsyn_r, B.gana_r, B.gana, B.hana, B.items, B.item_off, B.nu_dev};
         for (void* q : ptrs)
             if (q) cudaFree(q);
+        tc_batch_free(&B.tcb);
         if (B.P) sphnse_plan_destroy(B.P);
     }
     void* ptrs[] = {E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew, E->F, E->d_par, E->d_norms};
@@ -493,6 +503,29 @@ int sphnse_ensemble_set_stream(sphnse_ensemble* E, void* stream) {
     return SPHNSE_OK;
 }
 
+// BF16X3: the buckets whose grids the tensor-core kernels support get their
+// BF16 hi/lo tables, tensor maps and instance groups now (none of it may be
+// allocated while a graph is being captured); the captured graphs are rebuilt.
+static int set_precision(sphnse_ensemble* E, int prec) {
+    if (prec != SPHNSE_FP32 && prec != SPHNSE_BF16X3) return SPHNSE_E_UNSUPPORTED;
+    if (E->stream) cudaStreamSynchronize(E->stream);
+    for (auto& B : E->buckets) {
+        const bool want = prec == SPHNSE_BF16X3 && tc_supported(B.P);
+        if (want && !B.tcb.btiles) {
+            int rc = ensure_tables(B.P, SPHNSE_BF16X3);
+            if (!rc) rc = tc_setup_synthesis(B.P);
+            if (!rc) rc = tc_batch_init(B.P, B.nb, &B.tcb);
+            if (rc) return rc;
+        }
+        B.tc = want;
+    }
+    if (E->g_rhs_alpha) cudaGraphExecDestroy(E->g_rhs_alpha);
+    if (E->g_newton) cudaGraphExecDestroy(E->g_newton);
+    E->g_rhs_alpha = E->g_newton = nullptr;
+    E->precision = prec;
+    return SPHNSE_OK;
+}
+
 int sphnse_ensemble_set(sphnse_ensemble* E, int key, double v) {
     if (!E || !std::isfinite(v)) return SPHNSE_E_ARG;
     switch (key) {
@@ -501,7 +534,7 @@ int sphnse_ensemble_set(sphnse_ensemble* E, int key, double v) {
         case SPHNSE_KEY_MAX_ORDER: if (v < 1 || v > SPHNSE_MAXK) return SPHNSE_E_ARG; E->max_order = int(v); return SPHNSE_OK;
         case SPHNSE_KEY_NEWTON_MAX_ITER: if (v < 1 || v > 1000) return SPHNSE_E_ARG; E->newton_max = int(v); return SPHNSE_OK;
         case SPHNSE_KEY_H_MAX: if (v <= 0) return SPHNSE_E_ARG; E->h_max = v; return SPHNSE_OK;
-        case SPHNSE_KEY_PRECISION: return int(v) == SPHNSE_FP32 ? SPHNSE_OK : SPHNSE_E_UNSUPPORTED;
+        case SPHNSE_KEY_PRECISION: return set_precision(E, int(v));
         default: return SPHNSE_E_ARG;
     }
 }

@@ -89,6 +89,15 @@ struct Tables {
     bool built = false;
 };
 
+// Instance groups of a batched tcgen05 synthesis (one truncation): B tiles and
+// the LPT item schedule (m, latitude tile, group).
+struct TcBatch {
+    int nb = 0, ng = 0, ngroups = 0, brows = 0, ns = 0, ncta = 0;
+    unsigned char* btiles = nullptr;   // [group][tile][brows][64] bf16, swizzled
+    int4* items = nullptr;
+    int* off = nullptr;
+};
+
 // tcgen05 path state (tensor maps and item schedules, built on first use)
 struct TcState {
     void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
@@ -103,13 +112,10 @@ struct TcState {
     void* smap_lo = nullptr;
     void* tsyn_hi = nullptr;     // transposed padded bf16 tables [block][nh][pad8(n)]
     void* tsyn_lo = nullptr;
-    void* btiles = nullptr;      // synthesis B tiles [tile][16][64] bf16, swizzled (k_prep_tc)
-    int* tile_off = nullptr;     // first tile of block (m, parity)
+    int* tile_off = nullptr;     // first B tile of block (m, parity)
     int2* tile_info = nullptr;   // (block, K tile) of every B tile, in tile order
     int ntiles = 0;
-    int2* syn_items = nullptr;   // (m, latitude tile) per CTA (LPT)
-    int* syn_off = nullptr;
-    int syn_cta = 0;
+    TcBatch single;              // the plan's own instance
     size_t tsyn_bytes = 0;
     bool syn_ready = false;
 };
@@ -202,6 +208,12 @@ bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
 int launch_synthesis_tc(sphnse_plan* P, int pairs);
 int launch_prep_tc(sphnse_plan* P, const double* alpha);
+// batched tcgen05 synthesis over nb instances of P's truncation (ensembles)
+int tc_setup_synthesis(sphnse_plan* P);
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B);
+void tc_batch_free(TcBatch* B);
+int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha);
+int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs);
 // batched FP32 passes over instances of one truncation (ensemble)
 int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride);
 int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,

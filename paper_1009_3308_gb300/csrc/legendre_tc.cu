@@ -297,18 +297,19 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
 struct TcSynArgs {
     const CUtensorMap* map_hi;   // per (m, parity) block of the transposed tables
     const CUtensorMap* map_lo;
-    const int2* items;           // (m, latitude tile) per CTA (LPT)
+    const int4* items;           // (m, latitude tile, instance group, 0) per CTA (LPT)
     const int* item_off;
-    const unsigned char* btiles; // [tile][16][64] bf16, 128-byte swizzle (k_prep_tc)
+    const unsigned char* btiles; // [group][tile][brows][64] bf16, 128-byte swizzle (k_prep_tc)
     const int* tile_off;         // first tile of block b = 2 m + parity
-    float* gsyn;                 // [3][N+1][nlat] complex (m-major)
+    float* gsyn;                 // instance i writes gsyn + i * sgs complex entries
     const double* sinth;
     unsigned* status;
     int N, nh, nlat, nblk, pairs;
+    int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
+    size_t sgs;
 };
 
-constexpr int TC_SYN_COLS = 64;   // TMEM columns: 2 buffers x 2 parities x 16
-constexpr int TC_SYN_STAGE = 2 * TC_ATILE + TC_BTILE;
+constexpr int TC_SYN_MAXNS = 8;
 
 __host__ __device__ inline int syn_ndeg(int N, int m, int par) {
     const int n = par ? ext_odd(N, m) : ext_even(N, m);
@@ -323,26 +324,33 @@ __host__ __device__ inline int syn_tailw(int N, int m, int par) {
     return ((rem + 15) / 16) * 16;
 }
 
-// Item = (order m, latitude tile of 128 northern nodes): both parities into
-// their own accumulator (hi and lo table parts into the same one, as both
-// multiply the same B tile); K chunks of 16 degrees past the block are skipped.
+// Item = (order m, latitude tile of 128 northern nodes, group of ng
+// instances): both parities into their own accumulator of brows columns
+// (12 per instance: six hi parts, six lo parts of the coefficient sets; hi
+// and lo table parts go into the same accumulator, as both multiply the same
+// B tile), so one A tile serves every instance of the group.  K chunks of 16
+// degrees past the block are skipped.
 __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
+    const int ns = a.ns, brows = a.brows;
+    const int bbytes = brows * TC_TILE_K * 2;
     unsigned char* A_hi = smem;
-    unsigned char* A_lo = A_hi + TC_NS * TC_ATILE;
-    unsigned char* Bs = A_lo + TC_NS * TC_ATILE;                 // TC_NS x 2 KB
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + TC_NS * TC_BTILE);
+    unsigned char* A_lo = A_hi + ns * TC_ATILE;
+    unsigned char* Bs = A_lo + ns * TC_ATILE;                    // ns x brows x 128 B
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + ns * bbytes);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + TC_NS;
-    uint64_t* acc_full = bars + 2 * TC_NS;
+    uint64_t* a_empty = bars + ns;
+    uint64_t* acc_full = bars + 2 * ns;
     uint64_t* acc_empty = acc_full + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    uint32_t tcols = 32;
+    while (tcols < uint32_t(4 * brows)) tcols <<= 1;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_NS; ++s) {
+        for (int s = 0; s < ns; ++s) {
             mbar_init(&a_full[s], 1);
             mbar_init(&a_empty[s], 1);
         }
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, TC_SYN_COLS);
+        tmem_alloc(tmem_slot, tcols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -372,32 +380,33 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const uint64_t polb = policy_evict_last();
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int2 itm = a.items[ib + i];
-                const int m = itm.x, mt = itm.y;
+                const int4 itm = a.items[ib + i];
+                const int m = itm.x, mt = itm.y, g = itm.z;
                 for (int par = 0; par < 2; ++par) {
                     const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
                     const int tw = syn_tailw(N, m, par);
-                    const unsigned char* bsrc = a.btiles + size_t(a.tile_off[b]) * TC_BTILE;
+                    const unsigned char* bsrc =
+                        a.btiles + (size_t(g) * a.ntiles + size_t(a.tile_off[b])) * size_t(bbytes);
                     for (int kt = 0; kt < nkt; ++kt, ++it) {
-                        const int s = it % TC_NS;
-                        if (it >= TC_NS && !mbar_wait(&a_empty[s], ((it / TC_NS) - 1) & 1, abort, a.status)) continue;
+                        const int s = it % ns;
+                        if (it >= ns && !mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
                         if (*abort) continue;
                         const bool last = kt == nkt - 1;
                         const int w = last ? tw : TC_TILE_K;
                         const int mi = last ? a.nblk + b : b;
-                        mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2 + TC_BTILE));
+                        mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2 + bbytes));
                         tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
                         tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                        bulk_g2s(Bs + s * TC_BTILE, bsrc + size_t(kt) * TC_BTILE, TC_BTILE, &a_full[s], polb);
+                        bulk_g2s(Bs + s * bbytes, bsrc + size_t(kt) * bbytes, uint32_t(bbytes), &a_full[s], polb);
                     }
                 }
             }
-            for (int k = it - TC_NS; k < it; ++k)
-                if (k >= 0) mbar_wait(&a_full[k % TC_NS], (k / TC_NS) & 1, abort, a.status);
+            for (int k = it - ns; k < it; ++k)
+                if (k >= 0) mbar_wait(&a_full[k % ns], (k / ns) & 1, abort, a.status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(TC_TILE_M, TC_N);
+            const uint32_t idesc = idesc_bf16(TC_TILE_M, brows);
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int m = a.items[ib + i].x;
@@ -407,16 +416,16 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
                     const int nkt = syn_nkt(N, m, par), nd = syn_ndeg(N, m, par);
-                    const uint32_t d = tmem + uint32_t((buf * 2 + par) * TC_N);
+                    const uint32_t d = tmem + uint32_t((buf * 2 + par) * brows);
                     for (int kt = 0; kt < nkt; ++kt, ++it) {
-                        const int s = it % TC_NS;
-                        const bool okA = mbar_wait(&a_full[s], (it / TC_NS) & 1, abort, a.status);
+                        const int s = it % ns;
+                        const bool okA = mbar_wait(&a_full[s], (it / ns) & 1, abort, a.status);
                         tc_fence_after();
                         // 16-degree chunks of this K tile that hold degrees of the block
                         const int nkk = min(TC_TILE_K, nd - kt * TC_TILE_K + 15) / 16;
                         if (ok && okA && !*abort) {
                             for (int kk = 0; kk < nkk; ++kk) {
-                                const uint64_t bd = sdesc_sw128(Bs + s * TC_BTILE + kk * 32);
+                                const uint64_t bd = sdesc_sw128(Bs + s * bbytes + kk * 32);
                                 mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
                                 mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                             }
@@ -432,66 +441,78 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         pdl_wait();
         const int quarter = warp & 3;
         const size_t ld = size_t(N + 1);
+        (void)ld;
         for (int i = 0; i < nI; ++i) {
-            const int2 itm = a.items[ib + i];
-            const int m = itm.x, mt = itm.y, buf = i & 1;
+            const int4 itm = a.items[ib + i];
+            const int m = itm.x, mt = itm.y, g = itm.z, buf = i & 1;
+            const int ngi = min(a.ng, a.nb - g * a.ng);
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
             const float mm = float(m);
-            float e[16], o[16];
-            const uint32_t lanes = uint32_t(quarter * 32) << 16;
-            tmem_ld16(tmem + lanes + uint32_t((buf * 2 + 0) * TC_N), e);
-            tmem_ld16(tmem + lanes + uint32_t((buf * 2 + 1) * TC_N), o);
-            tc_fence_before();
-            mbar_arrive(&acc_empty[buf]);
             const int p = mt * TC_TILE_M + quarter * 32 + lane;
-            if (!ok || p >= nh || *abort) continue;
-            const float inv_s = float(1.0 / a.sinth[p]);
-            float E[6], O[6];
+            const uint32_t lanes = uint32_t(quarter * 32) << 16;
+            const float inv_s = p < nh ? float(1.0 / a.sinth[p]) : 0.f;
+            for (int q = 0; q < ngi; ++q) {
+                float e[12], o[12];
+                const uint32_t ce = tmem + lanes + uint32_t((buf * 2 + 0) * brows + 12 * q);
+                const uint32_t co = tmem + lanes + uint32_t((buf * 2 + 1) * brows + 12 * q);
+                tmem_ld8(ce, e);
+                tmem_ld4(ce + 8, e + 8);
+                tmem_ld8(co, o);
+                tmem_ld4(co + 8, o + 8);
+                if (!ok || p >= nh || *abort) continue;
+                float E[6], O[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                E[c] = e[c] + e[6 + c];
-                O[c] = o[c] + o[6 + c];
-            }
+                for (int c = 0; c < 6; ++c) {
+                    E[c] = e[c] + e[6 + c];
+                    O[c] = o[c] + o[6 + c];
+                }
+                float2* out = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
 #pragma unroll
-            for (int hemi = 0; hemi < 2; ++hemi) {
-                const int row = hemi == 0 ? p : nlat - 1 - p;
-                if (hemi == 1 && row == p) break;
-                const float sg = hemi == 0 ? 1.f : -1.f;
+                for (int hemi = 0; hemi < 2; ++hemi) {
+                    const int row = hemi == 0 ? p : nlat - 1 - p;
+                    if (hemi == 1 && row == p) break;
+                    const float sg = hemi == 0 ? 1.f : -1.f;
 #pragma unroll
-                for (int f = 0; f < 3; ++f) {
-                    const float gr = E[2 * f] + sg * O[2 * f];
-                    const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
-                    float2 ov;
-                    if (f == 0) ov = make_float2(gr, gi);
-                    else if (f == 1) ov = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
-                    else ov = make_float2(-gr * inv_s, -gi * inv_s);
-                    reinterpret_cast<float2*>(a.gsyn)[gsyn_index(a.pairs, f, m, row, N, nlat)] = ov;
+                    for (int f = 0; f < 3; ++f) {
+                        const float gr = E[2 * f] + sg * O[2 * f];
+                        const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
+                        float2 ov;
+                        if (f == 0) ov = make_float2(gr, gi);
+                        else if (f == 1) ov = make_float2(-mm * gi * inv_s, mm * gr * inv_s);
+                        else ov = make_float2(-gr * inv_s, -gi * inv_s);
+                        out[gsyn_index(a.pairs, f, m, row, N, nlat)] = ov;
+                    }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, TC_SYN_COLS);
+        tmem_dealloc(tmem, tcols);
     }
 }
 
 // Coefficient sets of the synthesis (zeta: lam^{1/2} a_K; theta: lam^{-1/2}
 // a_K; phi: c_down a_{K-1} + c_up a_{K+1}, the degree-shift form of
 // sin(theta) d/dtheta), written as the B tiles of k_syn_tc.  Thread (tile,
-// chunk q) of the flat tile list computes the 8 degrees K = m + par + 2 j,
+// chunk q) of instance blockIdx.y computes the 8 degrees K = m + par + 2 j,
 // j = 64 kt + 8 q .. +7, of block b = (m, parity), and stores the hi parts of
-// the six columns in rows 0-5 and the lo parts in rows 6-11 (rows 12-15 stay
-// zero).  All of a thread's loads are independent, so they overlap.
+// the six columns in rows r0 .. r0+5 and the lo parts in rows r0+6 .. r0+11,
+// r0 = 12 (instance mod ng), of its group's tile (rows past the group's
+// instances stay zero).  All of a thread's loads are independent.
 __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
                                                  unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
-                                                 int ntiles, int N) {
+                                                 int ntiles, int N, int n_coeff, int ng, int brows) {
     pdl_launch();
     const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
     if (g >= ntiles) return;
+    const int inst = blockIdx.y;
+    alpha += size_t(inst) * n_coeff;
     const int2 ti = tinfo[g];
     const int b = ti.x, kt = ti.y, m = b >> 1, par = b & 1;
     const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
@@ -522,11 +543,12 @@ __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alp
         v[4][e] = fmaf(cf[e].z, am.x, cf[e].w * ap.x);
         v[5][e] = fmaf(cf[e].z, am.y, cf[e].w * ap.y);
     }
-    unsigned char* tile = btiles + size_t(g) * TC_BTILE;
+    const int grp = inst / ng, row0 = 12 * (inst % ng);
+    unsigned char* tile = btiles + (size_t(grp) * ntiles + g) * size_t(brows) * TC_TILE_K * 2;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(c, q)) = pack_hi(v[c]);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(6 + c, q)) = pack_lo(v[c]);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + c, q)) = pack_hi(v[c]);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + 6 + c, q)) = pack_lo(v[c]);
     }
 }
 
@@ -552,7 +574,7 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool tc_supported(const sphnse_plan* P) { return P->nh % 8 == 0 && P->nh >= 64 && P->nlat % 2 == 0; }
+bool tc_supported(const sphnse_plan* P) { return P->nh % 8 == 0 && P->nh >= 16 && P->nlat % 2 == 0; }
 
 // Tensor maps over the whole [ext row][nh] bf16 tables, the analysis items
 // (128-row tiles split into groups of at most 32 / (4 NF) overlapped blocks)
@@ -738,13 +760,11 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemcpy(T.smap_hi, mh.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     cudaMemcpy(T.smap_lo, ml.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
-    // B tiles of the coefficient sets (k_prep_tc): one 2 KB tile per (m, parity, K tile)
+    // tile list of the B operand: one tile per (m, parity, K tile)
     std::vector<int> toff(nblk + 1, 0);
     for (int b = 0; b < nblk; ++b) toff[b + 1] = toff[b] + syn_nkt(N, b / 2, b % 2);
-    if (cudaMalloc(&T.btiles, size_t(toff[nblk]) * TC_BTILE) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&T.tile_off), toff.size() * sizeof(int)) != cudaSuccess)
+    if (cudaMalloc(reinterpret_cast<void**>(&T.tile_off), toff.size() * sizeof(int)) != cudaSuccess)
         return SPHNSE_E_NOMEM;
-    cudaMemset(T.btiles, 0, size_t(toff[nblk]) * TC_BTILE);
     cudaMemcpy(T.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
     {   // flat tile list (block, K tile) for k_prep_tc
         std::vector<int2> ti;
@@ -755,78 +775,120 @@ int tc_setup_synthesis(sphnse_plan* P) {
         cudaMemcpy(T.tile_info, ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice);
         T.ntiles = int(ti.size());
     }
-    // items (m, latitude tile), LPT on their stage counts (+1 for the epilogue)
-    {
-        const int nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
-        std::vector<int2> its;
-        std::vector<int> cost;
-        for (int m = 0; m <= N; ++m)
-            for (int mt = 0; mt < nmt; ++mt) {
-                its.push_back(make_int2(m, mt));
-                cost.push_back(syn_nkt(N, m, 0) + syn_nkt(N, m, 1) + 1);
-            }
-        std::vector<int> order(its.size());
-        for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-        const int G = std::min<int>(P->n_cta, int(its.size()));
-        std::vector<std::vector<int2>> bins(G);
-        std::vector<long> load(G, 0);
-        for (int idx : order) {
-            const int bb = int(std::min_element(load.begin(), load.end()) - load.begin());
-            bins[bb].push_back(its[idx]);
-            load[bb] += cost[idx];
-        }
-        std::vector<int2> flat;
-        std::vector<int> offs(1, 0);
-        for (auto& bi : bins) {
-            flat.insert(flat.end(), bi.begin(), bi.end());
-            offs.push_back(int(flat.size()));
-        }
-        if (cudaMalloc(reinterpret_cast<void**>(&T.syn_items), flat.size() * sizeof(int2)) != cudaSuccess ||
-            cudaMalloc(reinterpret_cast<void**>(&T.syn_off), offs.size() * sizeof(int)) != cudaSuccess)
-            return SPHNSE_E_NOMEM;
-        cudaMemcpy(T.syn_items, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice);
-        cudaMemcpy(T.syn_off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
-        T.syn_cta = G;
-    }
     T.tsyn_bytes = 2 * total * 2;
     T.syn_ready = true;
+    const int rc = tc_batch_init(P, 1, &T.single);
+    if (rc) return rc;
     return check_cuda(cudaGetLastError());
+}
+
+// Instance groups of a batch of nb instances of one truncation: ng <= 10
+// instances share every A tile (MMA N = brows = 12 ng rounded up to 16),
+// B tiles [group][tile][brows][64], items (m, latitude tile, group) in LPT
+// order over one CTA per SM.
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
+    if (nb < 1) return SPHNSE_E_ARG;
+    const int N = P->N, nh = P->nh;
+    TcBatch T;
+    T.nb = nb;
+    T.ng = std::min(nb, 10);
+    T.ngroups = (nb + T.ng - 1) / T.ng;
+    T.ng = (nb + T.ngroups - 1) / T.ngroups;   // balanced groups
+    T.brows = ((12 * T.ng + 15) / 16) * 16;
+    const size_t stage = 2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2;
+    T.ns = int(std::min<size_t>(6, (size_t(227) * 1024 - 1024 - 512) / stage));
+    const size_t bytes = size_t(T.ngroups) * P->tc.ntiles * T.brows * TC_TILE_K * 2;
+    if (cudaMalloc(reinterpret_cast<void**>(&T.btiles), bytes) != cudaSuccess) return SPHNSE_E_NOMEM;
+    cudaMemset(T.btiles, 0, bytes);
+    const int nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
+    std::vector<int4> its;
+    std::vector<double> cost;
+    for (int g = 0; g < T.ngroups; ++g) {
+        const int ngi = std::min(T.ng, nb - g * T.ng);
+        for (int m = 0; m <= N; ++m)
+            for (int mt = 0; mt < nmt; ++mt) {
+                its.push_back(make_int4(m, mt, g, 0));
+                // streamed stages (A and B bytes) plus the epilogue of the group
+                cost.push_back((syn_nkt(N, m, 0) + syn_nkt(N, m, 1)) * (1.0 + T.brows / 256.0) + 0.5 + 0.1 * ngi);
+            }
+    }
+    std::vector<int> order(its.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    const int G = std::min<int>(P->n_cta, int(its.size()));
+    std::vector<std::vector<int4>> bins(G);
+    std::vector<double> load(G, 0.0);
+    for (int idx : order) {
+        const int bb = int(std::min_element(load.begin(), load.end()) - load.begin());
+        bins[bb].push_back(its[idx]);
+        load[bb] += cost[idx];
+    }
+    std::vector<int4> flat;
+    std::vector<int> offs(1, 0);
+    for (auto& bi : bins) {
+        flat.insert(flat.end(), bi.begin(), bi.end());
+        offs.push_back(int(flat.size()));
+    }
+    if (cudaMalloc(reinterpret_cast<void**>(&T.items), flat.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.off), offs.size() * sizeof(int)) != cudaSuccess) {
+        tc_batch_free(&T);
+        return SPHNSE_E_NOMEM;
+    }
+    cudaMemcpy(T.items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    T.ncta = G;
+    *B = T;
+    return check_cuda(cudaGetLastError());
+}
+
+void tc_batch_free(TcBatch* B) {
+    for (void* q : {static_cast<void*>(B->btiles), static_cast<void*>(B->items), static_cast<void*>(B->off)})
+        if (q) cudaFree(q);
+    *B = TcBatch();
+}
+
+int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) {
+    stage_begin(P, SPHNSE_STAGE_PREP);
+    k_prep_tc<<<dim3((P->tc.ntiles + 15) / 16, B.nb), 128, 0, P->stream>>>(
+        reinterpret_cast<const double2*>(alpha), P->d_prepc32, B.btiles, P->tc.tile_info, P->tc.ntiles, P->N,
+        P->n_coeff, B.ng, B.brows);
+    stage_end(P, SPHNSE_STAGE_PREP);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs) {
+    const size_t sm = 1024 + size_t(B.ns) * (2 * size_t(TC_ATILE) + size_t(B.brows) * TC_TILE_K * 2) + 512;
+    if (sm > 227 * 1024 || B.ns > TC_SYN_MAXNS) return SPHNSE_E_UNSUPPORTED;
+    cudaFuncSetAttribute(k_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
+                reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
+                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
+                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2};
+    stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
+    const cudaError_t e = launch_pdl(k_syn_tc, dim3(B.ncta), dim3(192), sm, P->stream, a);
+    stage_end(P, SPHNSE_STAGE_SYNTHESIS);
+    return check_cuda(e);
 }
 
 int launch_prep_tc(sphnse_plan* P, const double* alpha) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
-    stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep_tc<<<(P->tc.ntiles + 15) / 16, 128, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
-                                                               P->d_prepc32, static_cast<unsigned char*>(P->tc.btiles),
-                                                               P->tc.tile_info, P->tc.ntiles, P->N);
-    stage_end(P, SPHNSE_STAGE_PREP);
-    return check_cuda(cudaGetLastError());
+    return launch_prep_tc_batch(P, P->tc.single, alpha);
 }
 
 int launch_synthesis_tc(sphnse_plan* P, int pairs) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
-    const size_t sm = 1024 + size_t(TC_NS) * TC_SYN_STAGE + 256;
-    if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
-                reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), P->tc.syn_items, P->tc.syn_off,
-                static_cast<const unsigned char*>(P->tc.btiles), P->tc.tile_off, reinterpret_cast<float*>(P->d_gsyn),
-                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs};
-    stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    const cudaError_t e = launch_pdl(k_syn_tc, dim3(P->tc.syn_cta), dim3(192), sm, P->stream, a);
-    stage_end(P, SPHNSE_STAGE_SYNTHESIS);
-    return check_cuda(e);
+    return launch_synthesis_tc_batch(P, P->tc.single, reinterpret_cast<float*>(P->d_gsyn), 0, pairs);
 }
 
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
     void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
-                    T.tsyn_lo, T.btiles, T.tile_off, T.syn_items, T.syn_off, T.tile_info};
+                    T.tsyn_lo, T.tile_off, T.tile_info};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    tc_batch_free(&T.single);
     T = TcState();
 }
 

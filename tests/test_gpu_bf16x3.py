@@ -2,11 +2,10 @@
 cores (FP32 accumulation), checked against the FP64 oracle.
 
 Error budget: each operand is split as x = hi + lo with hi, lo in BF16
-(8-bit significands), so |x - hi - lo| <= 2^-17 |x|; the product keeps
-hi*hi + hi*lo + lo*hi and drops lo*lo (<= 2^-16 relative); FP32
-accumulation adds ~2^-24 sqrt(n).  Per contraction output the relative
-error is ~1e-5 of the sum of |terms|; the tests take 1e-4 on F (norm) and
-state the measured error."""
+(8-bit significands), so |x - hi - lo| <= 2^-17 |x|; the products keep all
+four terms hi*hi + hi*lo + lo*hi + lo*lo; FP32 accumulation adds ~2^-24
+sqrt(n).  Per contraction output the relative error is ~1e-5 of the sum of
+|terms|; the tests take 1e-4 on F (norm) and state the measured error."""
 import numpy as np
 import pytest
 
@@ -26,7 +25,8 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("L,nlon,nu,Om,decay", [(127, 384, 1e-4, 1.0, 0.05), (255, 768, 1e-4, 1.0, 0.05)])
+@pytest.mark.parametrize("L,nlon,nu,Om,decay", [(31, 96, 1e-2, 1.0, 0.3), (63, 192, 1e-3, 1.0, 0.1),
+                                                (127, 384, 1e-4, 1.0, 0.05), (255, 768, 1e-4, 1.0, 0.05)])
 def test_rhs_bf16x3_matches_oracle(L, nlon, nu, Om, decay):
     from paper_1009_3308_gb300 import Plan
     prob = Problem(L, nlon, nu, Om)
@@ -53,3 +53,26 @@ def test_rhs_bf16x3_L511_vs_fp64():
     print(f"L=511 bf16x3 vs fp64 rel err {err:.3e}")
     assert err <= 1e-4, err
     assert plan.sync() == 0
+
+
+def test_ensemble_bf16x3_groups_match_fp64_plans():
+    """Batched tensor-core synthesis: 23 instances at L = 63 (three instance
+    groups sharing each table tile), three at 127 and two at 255; every
+    instance's F against a plan of its own in FP64."""
+    from paper_1009_3308_gb300 import Ensemble, Plan
+    Ls = [63] * 23 + [127] * 3 + [255] * 2
+    nus = [1e-3 * (0.9 ** i) for i in range(len(Ls))]
+    ens = Ensemble(Ls, nus, 1.0, precision="bf16x3")
+    alphas = [coefficients(L, 2000 + i, 0.05) * 3 for i, L in enumerate(Ls)]
+    for i, a in enumerate(alphas):
+        ens.set_alpha(i, _dev(a))
+    ens.rhs()
+    worst = 0.0
+    for i, (L, nu) in enumerate(zip(Ls, nus)):
+        M = 3 * (L + 1)
+        ref = Plan(L, M // 2, M, nu, 1.0).rhs(_dev(alphas[i])).cpu().numpy()
+        got = ens.get(i, "F").cpu().numpy()
+        err = _rel(got, ref)
+        worst = max(worst, err)
+        assert err <= 1e-4, (i, L, err)
+    print(f"ensemble bf16x3 worst rel err {worst:.3e}")
