@@ -205,6 +205,7 @@ struct Bucket {
     int ncta = 0;
     double* nu_dev = nullptr;
     TcBatch tcb;               // BF16X3: instance groups of the tensor-core synthesis
+    TcBatchA tca;              //         and slots of the tensor-core analysis
     bool tc = false;
 };
 
@@ -265,8 +266,11 @@ int batched_rhs(sphnse_ensemble* E, const double2* x, double2* F) {
             if ((rc = launch_ring_batch(P, B.nb, B.gsyn_r, B.sg, B.gana_r, B.sa))) return rc;
             if ((rc = launch_transpose(P, B.gana_r, B.gana, P->nlat, P->N + 1, 2 * B.nb, SPHNSE_FP32))) return rc;
         }
-        if ((rc = launch_analysis_stream_batch(P, B.items, B.item_off, B.ncta, B.gana, B.sa, B.hana, B.sh)))
+        if (B.tc) {
+            if ((rc = launch_analysis_tc_batch(P, B.tca, B.gana, B.sa, B.hana, B.sh))) return rc;
+        } else if ((rc = launch_analysis_stream_batch(P, B.items, B.item_off, B.ncta, B.gana, B.sa, B.hana, B.sh))) {
             return rc;
+        }
         if ((rc = launch_finish32_batch(P, B.nb, B.hana, B.sh, xb, Fb, B.nu_dev))) return rc;
     }
     return SPHNSE_OK;
@@ -323,6 +327,7 @@ void destroy_ens(sphnse_ensemble* E) {
         for (void* q : ptrs)
             if (q) cudaFree(q);
         tc_batch_free(&B.tcb);
+        tc_batch_ana_free(&B.tca);
         if (B.P) sphnse_plan_destroy(B.P);
     }
     void* ptrs[] = {E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew, E->F, E->d_par, E->d_norms};
@@ -515,6 +520,7 @@ static int set_precision(sphnse_ensemble* E, int prec) {
             int rc = ensure_tables(B.P, SPHNSE_BF16X3);
             if (!rc) rc = tc_setup_synthesis(B.P);
             if (!rc) rc = tc_batch_init(B.P, B.nb, &B.tcb);
+            if (!rc) rc = tc_batch_ana_init(B.P, B.nb, &B.tca);
             if (rc) return rc;
         }
         B.tc = want;

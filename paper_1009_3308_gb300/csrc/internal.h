@@ -98,6 +98,16 @@ struct TcBatch {
     int* off = nullptr;
 };
 
+// Batched tcgen05 analysis (NF = 2) over nb instances of one truncation:
+// items (tile, slots of (block, instance)) and the per-instance S tiles.
+struct TcBatchA {
+    int nb = 0, nkt = 0, ncta = 0;
+    int4* items = nullptr;
+    int* off = nullptr;
+    int4* slots = nullptr;
+    unsigned char* stiles = nullptr;   // [instance][block][kt] 1 KB
+};
+
 // tcgen05 path state (tensor maps and item schedules, built on first use)
 struct TcState {
     void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
@@ -214,6 +224,11 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B);
 void tc_batch_free(TcBatch* B);
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha);
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs);
+int tc_setup_analysis(sphnse_plan* P, int nf);
+int tc_batch_ana_init(sphnse_plan* P, int nb, TcBatchA* B);
+void tc_batch_ana_free(TcBatchA* B);
+int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gana, size_t sa_floats, float* hana,
+                             size_t sh_floats);
 // batched FP32 passes over instances of one truncation (ensemble)
 int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride);
 int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* item_off, int ncta,

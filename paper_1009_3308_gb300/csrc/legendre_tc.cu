@@ -35,12 +35,10 @@
 
 namespace sph {
 
-constexpr int TC_NS = 6;          // A pipeline stages
 constexpr int TC_TILE_M = 128;    // rows per MMA tile
 constexpr int TC_TILE_K = 64;     // K per smem tile (128 bytes of bf16)
 constexpr int TC_N = 16;          // accumulator columns (B rows)
 constexpr int TC_ATILE = TC_TILE_M * TC_TILE_K * 2;   // 16 KB
-constexpr int TC_BTILE = TC_N * TC_TILE_K * 2;        // 2 KB
 
 // 8 bf16 (hi or lo parts of v[0..7]) packed for one 16-byte swizzle chunk
 __device__ __forceinline__ uint4 pack_hi(const float* v) {
@@ -281,6 +279,200 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, TC_ANA_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batched analysis (instances of one truncation)
+//
+// k_ana_prep writes, per instance, block (m, parity) and K tile of 64
+// latitudes, the B rows of the analysis as one 1 KB swizzled tile: rows
+// 2f, 2f+1 = hi parts of Re, Im of S_f(p) = G_f(p) +- G_f(p') (the
+// hemispheric sum for even, difference for odd K - m), rows 4+2f, 5+2f = lo
+// parts.  Eight rows make one 128-byte swizzle atom, so the tile is valid at
+// any 8-row offset of a B operand.
+// k_ana_tc_b streams each 128-row tile of consecutive table rows once per
+// item = (tile, <= 32 slots of (overlapped block, instance)); each stage
+// brings A_hi, A_lo by TMA and the slots' S tiles by bulk copy into rows
+// 8 slot .. 8 slot + 7 of B, so one MMA (N = 8 slots) serves every slot.
+
+__global__ void __launch_bounds__(128) k_ana_prep(const float* __restrict__ gana, size_t sa, unsigned char* __restrict__ stiles,
+                                                  int N, int nh, int nlat, int nkt) {
+    pdl_launch();
+    pdl_wait();
+    const int inst = blockIdx.y;
+    const int nblk = 2 * (N + 1);
+    const int t = blockIdx.x * 128 + threadIdx.x;   // (block, kt, q, f)
+    if (t >= nblk * nkt * 16) return;
+    const int f = t & 1, q = (t >> 1) & 7, kt = (t >> 4) % nkt, b = (t >> 4) / nkt;
+    const int m = b >> 1, par = b & 1;
+    const float* g = gana + size_t(inst) * sa + (size_t(f) * (N + 1) + m) * size_t(nlat) * 2;
+    const int p0 = kt * TC_TILE_K + q * 8;
+    float re[8], im[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int p = p0 + e;
+        float nr = 0.f, ni = 0.f, sr = 0.f, si = 0.f;
+        if (p < nh) {
+            nr = g[2 * size_t(p)];
+            ni = g[2 * size_t(p) + 1];
+            const int pr = nlat - 1 - p;
+            if (pr != p) {
+                sr = g[2 * size_t(pr)];
+                si = g[2 * size_t(pr) + 1];
+            }
+        }
+        re[e] = par ? nr - sr : nr + sr;
+        im[e] = par ? ni - si : ni + si;
+    }
+    unsigned char* tile = stiles + ((size_t(inst) * nblk + b) * nkt + kt) * 1024;
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f, q)) = pack_hi(re);
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f + 1, q)) = pack_hi(im);
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(4 + 2 * f, q)) = pack_lo(re);
+    *reinterpret_cast<uint4*>(tile + sw128_chunk(5 + 2 * f, q)) = pack_lo(im);
+}
+
+struct TcAnaBArgs {
+    const CUtensorMap* map_hi;   // whole table [n_ext][nh], box 64 x 128
+    const CUtensorMap* map_lo;
+    const int4* items;           // (tile, first slot, slot count, N)
+    const int* item_off;
+    const int4* slots;           // (m, parity, instance, rows s | e << 16 within the tile)
+    const unsigned char* stiles; // [instance][block][kt] 1 KB
+    float* hana;                 // instance i: hana + i * sh floats, [n_ext][4]
+    size_t sh;
+    unsigned* status;
+    int N, nkt, n_ext;
+};
+
+constexpr int TC_ANAB_NS = 3;                  // stages of A (32 KB) + B (<= 32 KB)
+constexpr int TC_ANAB_BBYTES = 256 * 128;      // B: up to 256 rows
+
+__global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~uintptr_t(1023));
+    unsigned char* A_hi = smem;
+    unsigned char* A_lo = A_hi + TC_ANAB_NS * TC_ATILE;
+    unsigned char* Bs = A_lo + TC_ANAB_NS * TC_ATILE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + TC_ANAB_NS * TC_ANAB_BBYTES);
+    uint64_t* a_full = bars;
+    uint64_t* a_empty = bars + TC_ANAB_NS;
+    uint64_t* acc_full = bars + 2 * TC_ANAB_NS;
+    uint64_t* acc_empty = acc_full + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 4);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int nkt = a.nkt, nblk = 2 * (a.N + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_ANAB_NS; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        *abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    pdl_launch();
+    const uint32_t tmem = *tmem_slot;
+    const int ib = a.item_off[blockIdx.x], nI = a.item_off[blockIdx.x + 1] - ib;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            pdl_wait();
+            const uint64_t pol = policy_evict_first();
+            const uint64_t polb = policy_evict_last();
+            int it = 0;
+            for (int i = 0; i < nI; ++i) {
+                const int4 itm = a.items[ib + i];
+                for (int kt = 0; kt < nkt; ++kt, ++it) {
+                    const int s = it % TC_ANAB_NS;
+                    if (it >= TC_ANAB_NS && !mbar_wait(&a_empty[s], ((it / TC_ANAB_NS) - 1) & 1, abort, a.status))
+                        continue;
+                    if (*abort) continue;
+                    mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * TC_ATILE + itm.z * 1024));
+                    tma_load_2d(A_hi + s * TC_ATILE, a.map_hi, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
+                    tma_load_2d(A_lo + s * TC_ATILE, a.map_lo, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
+                    for (int j = 0; j < itm.z; ++j) {
+                        const int4 sl = a.slots[itm.y + j];
+                        const unsigned char* src = a.stiles + ((size_t(sl.z) * nblk + 2 * sl.x + sl.y) * nkt + kt) * 1024;
+                        bulk_g2s(Bs + s * TC_ANAB_BBYTES + j * 1024, src, 1024, &a_full[s], polb);
+                    }
+                }
+            }
+            for (int k = it - TC_ANAB_NS; k < it; ++k)
+                if (k >= 0) mbar_wait(&a_full[k % TC_ANAB_NS], (k / TC_ANAB_NS) & 1, abort, a.status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0;
+            for (int i = 0; i < nI; ++i) {
+                const int4 itm = a.items[ib + i];
+                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w);
+                const int buf = i & 1, use = i >> 1;
+                bool ok = true;
+                if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
+                tc_fence_after();
+                const uint32_t d = tmem + uint32_t(buf * 256);
+                for (int kt = 0; kt < nkt; ++kt, ++it) {
+                    const int s = it % TC_ANAB_NS;
+                    const bool okA = mbar_wait(&a_full[s], (it / TC_ANAB_NS) & 1, abort, a.status);
+                    tc_fence_after();
+                    if (ok && okA && !*abort) {
+#pragma unroll
+                        for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
+                            const uint64_t bd = sdesc_sw128(Bs + s * TC_ANAB_BBYTES + kk * 32);
+                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
+                        }
+                    }
+                    mma_commit(&a_empty[s]);
+                }
+                mma_commit(&acc_full[buf]);
+            }
+            if (nI > 0) mbar_wait(&acc_full[(nI - 1) & 1], ((nI - 1) >> 1) & 1, abort, a.status);
+        }
+    } else {
+        // epilogue: slot j of the item -> columns 8 j .. 8 j + 7 (hi, then lo parts)
+        pdl_wait();
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;
+        for (int i = 0; i < nI; ++i) {
+            const int4 itm = a.items[ib + i];
+            const int buf = i & 1;
+            const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
+            tc_fence_after();
+            const int row = itm.x * TC_TILE_M + r;
+            for (int j = 0; j < itm.z; ++j) {
+                const int4 sl = a.slots[itm.y + j];
+                const int rs = sl.w & 0xFFFF, re = sl.w >> 16;
+                if (re <= quarter * 32 || rs >= quarter * 32 + 32) continue;   // warp-uniform
+                float v[8];
+                tmem_ld8(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * 256 + 8 * j), v);
+                if (ok && r >= rs && r < re && row < a.n_ext && !*abort) {
+                    float4 h = make_float4(v[0] + v[4], v[1] + v[5], v[2] + v[6], v[3] + v[7]);
+                    *reinterpret_cast<float4*>(a.hana + size_t(sl.z) * a.sh + size_t(row) * 4) = h;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -880,6 +1072,113 @@ int launch_synthesis_tc(sphnse_plan* P, int pairs) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
     return launch_synthesis_tc_batch(P, P->tc.single, reinterpret_cast<float*>(P->d_gsyn), 0, pairs);
+}
+
+// pieces of every 128-row tile of the [ext row] table: the blocks (m, parity)
+// overlapping rows [128 T, 128 T + 128), with their tile-row range
+static std::vector<std::vector<int4>> tile_pieces(int N, int n_ext) {
+    const int ntile = (n_ext + TC_TILE_M - 1) / TC_TILE_M;
+    std::vector<std::vector<int4>> per(ntile);
+    for (int m = 0; m <= N; ++m)
+        for (int par = 0; par < 2; ++par) {
+            const int ne = ext_even(N, m);
+            const int r0 = ext_off(N, m) + (par ? ne : 0), nr = par ? ext_odd(N, m) : ne;
+            for (int r = r0; r < r0 + nr;) {
+                const int tt = r / TC_TILE_M, end = std::min(r0 + nr, (tt + 1) * TC_TILE_M);
+                per[tt].push_back(make_int4(m, par, r - tt * TC_TILE_M, end - tt * TC_TILE_M));
+                r = end;
+            }
+        }
+    return per;
+}
+
+// Batched analysis of nb instances (NF = 2): items (tile, <= 32 slots of
+// (block, instance)), LPT over one CTA per SM, and the S-tile buffer.
+int tc_batch_ana_init(sphnse_plan* P, int nb, TcBatchA* B) {
+    int rc = tc_setup_analysis(P, 2);
+    if (rc) return rc;
+    const int N = P->N, nh = P->nh;
+    TcBatchA T;
+    T.nb = nb;
+    T.nkt = (nh + TC_TILE_K - 1) / TC_TILE_K;
+    const auto per = tile_pieces(N, P->n_ext);
+    std::vector<int4> items, slots;
+    std::vector<double> cost;
+    for (int tt = 0; tt < int(per.size()); ++tt) {
+        const int np = int(per[tt].size());
+        const int ni = std::max(1, 32 / std::max(np, 1));
+        for (int j0 = 0; j0 < np; j0 += 32)   // a tile with more than 32 pieces: one instance, 32 pieces per item
+            for (int i0 = 0; i0 < nb; i0 += (np > 32 ? 1 : ni)) {
+                const int jn = std::min(32, np - j0);
+                const int in = np > 32 ? 1 : std::min(ni, nb - i0);
+                const int first = int(slots.size());
+                for (int j = j0; j < j0 + jn; ++j)
+                    for (int k = i0; k < i0 + in; ++k) {
+                        const int4 pc = per[tt][j];
+                        slots.push_back(make_int4(pc.x, pc.y, k, pc.z | (pc.w << 16)));
+                    }
+                const int ns = int(slots.size()) - first;
+                items.push_back(make_int4(tt, first, ns, ((8 * ns + 15) / 16) * 16));
+                cost.push_back(T.nkt * (1.0 + ns / 32.0) + 0.2 * ns);
+            }
+    }
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    const int G = std::min<int>(P->n_cta, int(items.size()));
+    std::vector<std::vector<int4>> bins(G);
+    std::vector<double> load(G, 0.0);
+    for (int idx : order) {
+        const int bb = int(std::min_element(load.begin(), load.end()) - load.begin());
+        bins[bb].push_back(items[idx]);
+        load[bb] += cost[idx];
+    }
+    std::vector<int4> flat;
+    std::vector<int> offs(1, 0);
+    for (auto& bi : bins) {
+        flat.insert(flat.end(), bi.begin(), bi.end());
+        offs.push_back(int(flat.size()));
+    }
+    const size_t sbytes = size_t(nb) * 2 * (N + 1) * T.nkt * 1024;
+    if (cudaMalloc(reinterpret_cast<void**>(&T.items), flat.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.off), offs.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.slots), slots.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.stiles), sbytes) != cudaSuccess) {
+        tc_batch_ana_free(&T);
+        return SPHNSE_E_NOMEM;
+    }
+    cudaMemcpy(T.items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.slots, slots.data(), slots.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    T.ncta = G;
+    *B = T;
+    return check_cuda(cudaGetLastError());
+}
+
+void tc_batch_ana_free(TcBatchA* B) {
+    for (void* q : {static_cast<void*>(B->items), static_cast<void*>(B->off), static_cast<void*>(B->slots),
+                    static_cast<void*>(B->stiles)})
+        if (q) cudaFree(q);
+    *B = TcBatchA();
+}
+
+int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gana, size_t sa_floats, float* hana,
+                             size_t sh_floats) {
+    const int nblk = 2 * (P->N + 1);
+    const size_t sm = 1024 + size_t(TC_ANAB_NS) * (2 * size_t(TC_ATILE) + TC_ANAB_BBYTES) + 512;
+    if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
+    stage_begin(P, SPHNSE_STAGE_ANALYSIS);
+    cudaError_t e = launch_pdl(k_ana_prep, dim3((nblk * B.nkt * 16 + 127) / 128, B.nb), dim3(128), 0, P->stream, gana,
+                               sa_floats, B.stiles, P->N, P->nh, P->nlat, B.nkt);
+    if (e == cudaSuccess) {
+        cudaFuncSetAttribute(k_ana_tc_b, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        TcAnaBArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi),
+                     reinterpret_cast<const CUtensorMap*>(P->tc.map_lo), B.items, B.off, B.slots, B.stiles, hana,
+                     sh_floats, P->d_status, P->N, B.nkt, P->n_ext};
+        e = launch_pdl(k_ana_tc_b, dim3(B.ncta), dim3(192), sm, P->stream, a);
+    }
+    stage_end(P, SPHNSE_STAGE_ANALYSIS);
+    return check_cuda(e);
 }
 
 void tc_free(sphnse_plan* P) {
