@@ -256,13 +256,15 @@ def extra_adjoint(torch, nsteps=40, checkpoint=20):
             "grad_norm": float(a0r.grad.norm()), "dJ_dnu": float(nut.grad)}
 
 
-def extra_ensemble(torch, nsteps=3, n=256):
+def extra_ensemble(torch, nsteps=3, n=256, precision="fp32"):
     """Batched ensemble: 256 instances, L uniform over {63, 127, 255}, nu
-    log-uniform in [1e-5, 1e-3], per-instance adaptive steps (FP32 path)."""
+    log-uniform in [1e-5, 1e-3], per-instance adaptive steps; "fp32"
+    streaming contractions or "bf16x3" (instances of a truncation share every
+    table tile on the tensor cores)."""
     from paper_1009_3308_gb300 import Ensemble
     from seeded_inputs import ensemble
     mem = ensemble(n)
-    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0)
+    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0, precision=precision)
     for i, m in enumerate(mem):
         ens.set_alpha(i, torch.from_numpy(m["alpha0"]))
     ens.set("RTOL", 1e-6)
@@ -274,7 +276,7 @@ def extra_ensemble(torch, nsteps=3, n=256):
     rhs = sum(sum(i["rhs_evals"] for i in inf) for inf in infos)
     return {"instance_steps_per_s": n * nsteps / el, "instance_rhs_per_s_in_steps": rhs / el,
             "batched_rhs_per_s": 3 / tr, "instance_rhs_per_s_batched": 3 * n / tr, "instances": n,
-            "steps": nsteps, "buckets": sorted(set(m["L"] for m in mem))}
+            "steps": nsteps, "buckets": sorted(set(m["L"] for m in mem)), "precision": precision}
 
 
 def cpu_baseline(w, target_s=15.0):
@@ -445,7 +447,9 @@ def main():
         if "fp64" in extras:
             extras["speedup_vs_fp64"] = value / world / extras["fp64"]["rhs_per_s"]
         for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)), ("adjoint_L255", lambda: extra_adjoint(torch)),
-                         ("ensemble", lambda: extra_ensemble(torch)), ("L31_fp64_steps", lambda: extra_L31(torch))):
+                         ("ensemble", lambda: extra_ensemble(torch)),
+                         ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),
+                         ("L31_fp64_steps", lambda: extra_L31(torch))):
             try:
                 extras[name] = fn()
             except Exception as e:  # an extra must not hide the headline line
