@@ -522,11 +522,15 @@ __host__ __device__ inline int syn_tailw(int N, int m, int par) {
 // and lo table parts go into the same accumulator, as both multiply the same
 // B tile), so one A tile serves every instance of the group.  K chunks of 16
 // degrees past the block are skipped.
+// NS stages (a compile-time ring keeps the per-stage index arithmetic of the
+// single-thread producer and MMA issuer cheap); SINGLE: one instance, 16 B rows
+template <int NS, bool SINGLE>
 __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
-    const int ns = a.ns, brows = a.brows;
+    constexpr int ns = NS;
+    const int brows = SINGLE ? 16 : a.brows;
     const int bbytes = brows * TC_TILE_K * 2;
     unsigned char* A_hi = smem;
     unsigned char* A_lo = A_hi + ns * TC_ATILE;
@@ -637,7 +641,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
             const int m = itm.x, mt = itm.y, g = itm.z, buf = i & 1;
-            const int ngi = min(a.ng, a.nb - g * a.ng);
+            const int ngi = SINGLE ? 1 : min(a.ng, a.nb - g * a.ng);
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
             const float mm = float(m);
@@ -645,19 +649,20 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const uint32_t lanes = uint32_t(quarter * 32) << 16;
             const float inv_s = p < nh ? float(1.0 / a.sinth[p]) : 0.f;
             for (int q = 0; q < ngi; ++q) {
-                float e[12], o[12];
+                uint32_t e[12], o[12];
                 const uint32_t ce = tmem + lanes + uint32_t((buf * 2 + 0) * brows + 12 * q);
                 const uint32_t co = tmem + lanes + uint32_t((buf * 2 + 1) * brows + 12 * q);
-                tmem_ld8(ce, e);
-                tmem_ld4(ce + 8, e + 8);
-                tmem_ld8(co, o);
-                tmem_ld4(co + 8, o + 8);
+                tmem_ld8_nowait(ce, e);
+                tmem_ld4_nowait(ce + 8, e + 8);
+                tmem_ld8_nowait(co, o);
+                tmem_ld4_nowait(co + 8, o + 8);
+                tmem_wait_ld();
                 if (!ok || p >= nh || *abort) continue;
                 float E[6], O[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    E[c] = e[c] + e[6 + c];
-                    O[c] = o[c] + o[6 + c];
+                    E[c] = __uint_as_float(e[c]) + __uint_as_float(e[6 + c]);
+                    O[c] = __uint_as_float(o[c]) + __uint_as_float(o[6 + c]);
                 }
                 float2* out = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
 #pragma unroll
@@ -1000,8 +1005,8 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
         for (int m = 0; m <= N; ++m)
             for (int mt = 0; mt < nmt; ++mt) {
                 its.push_back(make_int4(m, mt, g, 0));
-                // streamed stages (A and B bytes) plus the epilogue of the group
-                cost.push_back((syn_nkt(N, m, 0) + syn_nkt(N, m, 1)) * (1.0 + T.brows / 256.0) + 0.5 + 0.1 * ngi);
+                // streamed stages (A and B bytes) plus a fixed cost per item and the epilogue of the group
+                cost.push_back((syn_nkt(N, m, 0) + syn_nkt(N, m, 1)) * (1.0 + T.brows / 256.0) + 1.0 + 0.1 * (ngi - 1));
             }
     }
     std::vector<int> order(its.size());
@@ -1051,13 +1056,17 @@ int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) 
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs) {
     const size_t sm = 1024 + size_t(B.ns) * (2 * size_t(TC_ATILE) + size_t(B.brows) * TC_TILE_K * 2) + 512;
     if (sm > 227 * 1024 || B.ns > TC_SYN_MAXNS) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    const bool single = B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6;
+    auto kern = single ? k_syn_tc<6, true> : B.ns == 6 ? k_syn_tc<6, false> : B.ns == 5 ? k_syn_tc<5, false>
+                                                                            : k_syn_tc<4, false>;
+    if (!single && (B.ns < 4 || B.ns > 6)) return SPHNSE_E_UNSUPPORTED;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
                 P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
                 B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    const cudaError_t e = launch_pdl(k_syn_tc, dim3(B.ncta), dim3(192), sm, P->stream, a);
+    const cudaError_t e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(e);
 }
