@@ -388,31 +388,39 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
     const int ib = a.item_off[blockIdx.x], nI = a.item_off[blockIdx.x + 1] - ib;
 
     if (warp == 0) {
-        if (lane == 0) {
-            pdl_wait();
-            const uint64_t pol = policy_evict_first();
-            const uint64_t polb = policy_evict_last();
-            int it = 0;
-            for (int i = 0; i < nI; ++i) {
-                const int4 itm = a.items[ib + i];
-                for (int kt = 0; kt < nkt; ++kt, ++it) {
-                    const int s = it % TC_ANAB_NS;
-                    if (it >= TC_ANAB_NS && !mbar_wait(&a_empty[s], ((it / TC_ANAB_NS) - 1) & 1, abort, a.status))
-                        continue;
-                    if (*abort) continue;
-                    mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * TC_ATILE + itm.z * 1024));
+        // lane 0 waits for the slot and posts the byte count; every lane then
+        // issues the bulk copy of one slot's S tile (lane 0 also the A tiles)
+        pdl_wait();
+        const uint64_t pol = policy_evict_first();
+        const uint64_t polb = policy_evict_last();
+        int it = 0;
+        for (int i = 0; i < nI; ++i) {
+            const int4 itm = a.items[ib + i];
+            int4 sl = make_int4(0, 0, 0, 0);
+            if (lane < itm.z) sl = a.slots[itm.y + lane];
+            for (int kt = 0; kt < nkt; ++kt, ++it) {
+                const int s = it % TC_ANAB_NS;
+                int go = 0;
+                if (lane == 0) {
+                    const bool ok = it < TC_ANAB_NS || mbar_wait(&a_empty[s], ((it / TC_ANAB_NS) - 1) & 1, abort, a.status);
+                    go = ok && !*abort;
+                    if (go) mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * TC_ATILE + itm.z * 1024));
+                }
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (!go) continue;
+                if (lane == 0) {
                     tma_load_2d(A_hi + s * TC_ATILE, a.map_hi, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
                     tma_load_2d(A_lo + s * TC_ATILE, a.map_lo, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
-                    for (int j = 0; j < itm.z; ++j) {
-                        const int4 sl = a.slots[itm.y + j];
-                        const unsigned char* src = a.stiles + ((size_t(sl.z) * nblk + 2 * sl.x + sl.y) * nkt + kt) * 1024;
-                        bulk_g2s(Bs + s * TC_ANAB_BBYTES + j * 1024, src, 1024, &a_full[s], polb);
-                    }
+                }
+                if (lane < itm.z) {
+                    const unsigned char* src = a.stiles + ((size_t(sl.z) * nblk + 2 * sl.x + sl.y) * nkt + kt) * 1024;
+                    bulk_g2s(Bs + s * TC_ANAB_BBYTES + lane * 1024, src, 1024, &a_full[s], polb);
                 }
             }
+        }
+        if (lane == 0)
             for (int k = it - TC_ANAB_NS; k < it; ++k)
                 if (k >= 0) mbar_wait(&a_full[k % TC_ANAB_NS], (k / TC_ANAB_NS) & 1, abort, a.status);
-        }
     } else if (warp == 1) {
         if (lane == 0) {
             int it = 0;
