@@ -299,6 +299,15 @@ def cpu_baseline(w, target_s=15.0):
                       f"Legendre tables built before timing), {el:.1f} s"}
 
 
+def arm_config(c, prec, world):
+    """The workload both arms report (the reference arm times the oracle on it)."""
+    return {"workload": "L=511 RHS evaluation, 768x1536 Gauss-rectangle grid, "
+                        "seeded spectrum exp(-0.02 L)/(L(L+1)), nu=5e-5, Omega=1",
+            "L": c["L"], "nlat": c["nlat"], "nlon": c["nlon"], "precision": prec,
+            "l2": "inputs larger than L2 (Legendre tables streamed every step)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,8 +333,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "L=511 RHS, 768x1536 Gauss-rectangle grid, FP64 CPU oracle",
-                       "L": 511, "nlat": 768, "nlon": 1536},
+            "config": arm_config(c, args.precision or _best_mixed(), world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{steps} full RHS evaluations at L=511 (numpy FP64 oracle)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -465,11 +473,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32acc", "fp64": "f64"}[prec],
                 "data": "synthetic",
-                "config": {"workload": "L=511 RHS evaluation, 768x1536 Gauss-rectangle grid, "
-                                       "seeded spectrum exp(-0.02 L)/(L(L+1)), nu=5e-5, Omega=1",
-                           "L": L, "nlat": nlat, "nlon": nlon, "precision": prec,
-                           "l2": "inputs larger than L2 (Legendre tables streamed every step)",
-                           "parallelism": f"replicas x{world}"},
+                "config": arm_config(c, prec, world),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "stage_us_per_rhs": split, **extras}
         print(json.dumps(line), flush=True)
