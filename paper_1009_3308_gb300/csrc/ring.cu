@@ -510,13 +510,16 @@ __global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
     float2* XA = buf + r * RING;
     float2* XB = buf + (G + r) * RING;
 
-    // pass 1: Hermitian spectra packed as A = zeta + i u_theta, B = u_phi
+    // pass 1: Hermitian spectra packed as A = zeta + i u_theta, B = u_phi.
+    // With M >= 3N + 2, n = t + M2 n1 lies in (N, M - N) for n1 = 8 .. 15, so
+    // those inputs are zero for every thread (compile-time, folded into dft24)
     cx<float> xa[24], xb[24];
 #pragma unroll
     for (int n1 = 0; n1 < 24; ++n1) {
         const int n = t + M2 * n1;
         cx<float> za{0.f, 0.f}, zb{0.f, 0.f};
-        if (n <= N) {
+        if (n1 >= 8 && n1 < 16) {
+        } else if (n <= N) {
             float2 g0 = XA[n], g1 = XA[ld + n], g2 = XA[2 * ld + n];
             if (n == 0) g0.y = g1.y = g2.y = 0.f;
             za = {g0.x - g1.y, g0.y + g1.x};
@@ -648,8 +651,10 @@ __global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
     for (int k1 = 0; k1 < 24; ++k1) y[k1] = ld2(&XA[k1 * P1 + t]);
     dft24<-1>(y);
     __syncthreads();
+    // only m <= N and m >= M - N are read back: n1 = 8 .. 15 are never needed
 #pragma unroll
-    for (int n1 = 0; n1 < 24; ++n1) st2(&XA[t + M2 * n1], y[n1]);
+    for (int n1 = 0; n1 < 24; ++n1)
+        if (n1 < 8 || n1 >= 16) st2(&XA[t + M2 * n1], y[n1]);
     __syncthreads();
 
     // separate the two real fields, truncate to m <= N, weight, store
