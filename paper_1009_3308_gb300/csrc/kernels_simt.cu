@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(128) k_prep32(const double2* __restrict__ alph
                                                 int nf, int ncoef, size_t bstride) {
     __shared__ float2 sa[130], sb[130];
     pdl_launch();
+    pdl_wait();   // alpha may be the predecessor's output
     // batch of instances along gridDim.z (fixed strides between instances)
     alpha += size_t(blockIdx.z) * ncoef;
     if (beta) beta += size_t(blockIdx.z) * ncoef;
@@ -348,9 +349,9 @@ int launch_prep(sphnse_plan* P, const double* alpha, const double* beta, int pre
     const int nf = beta ? 5 : 3;
     dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1);
     stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep32<<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
-                                         reinterpret_cast<const double2*>(beta), P->d_prepc32,
-                                         reinterpret_cast<float*>(P->d_bsyn), P->N, nf, P->n_coeff, 0);
+    launch_pdl(k_prep32, grd, blk, 0, P->stream, reinterpret_cast<const double2*>(alpha),
+               reinterpret_cast<const double2*>(beta), static_cast<const float4*>(P->d_prepc32),
+               reinterpret_cast<float*>(P->d_bsyn), P->N, nf, P->n_coeff, size_t(0));
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
@@ -428,8 +429,9 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
 int launch_prep32_batch(sphnse_plan* P, int nb, const double* alpha, float* bsyn, size_t bstride) {
     dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1, nb);
     stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep32<<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha), nullptr, P->d_prepc32, bsyn,
-                                         P->N, 3, P->n_coeff, bstride);
+    launch_pdl(k_prep32, grd, blk, 0, P->stream, reinterpret_cast<const double2*>(alpha),
+               static_cast<const double2*>(nullptr), static_cast<const float4*>(P->d_prepc32), bsyn, P->N, 3,
+               P->n_coeff, bstride);
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }

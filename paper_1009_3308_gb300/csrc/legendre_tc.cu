@@ -714,6 +714,7 @@ __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alp
                                                  unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
                                                  int ntiles, int N, int n_coeff, int ng, int brows) {
     pdl_launch();
+    pdl_wait();   // alpha may be the predecessor's output
     const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
     if (g >= ntiles) return;
     const int inst = blockIdx.y;
@@ -1054,11 +1055,12 @@ void tc_batch_free(TcBatch* B) {
 
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) {
     stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep_tc<<<dim3((P->tc.ntiles + 15) / 16, B.nb), 128, 0, P->stream>>>(
-        reinterpret_cast<const double2*>(alpha), P->d_prepc32, B.btiles, P->tc.tile_info, P->tc.ntiles, P->N,
-        P->n_coeff, B.ng, B.brows);
+    const cudaError_t e = launch_pdl(k_prep_tc, dim3((P->tc.ntiles + 15) / 16, B.nb), dim3(128), 0, P->stream,
+                                     reinterpret_cast<const double2*>(alpha), static_cast<const float4*>(P->d_prepc32),
+                                     B.btiles, static_cast<const int2*>(P->tc.tile_info), P->tc.ntiles, P->N,
+                                     P->n_coeff, B.ng, B.brows);
     stage_end(P, SPHNSE_STAGE_PREP);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs) {
