@@ -196,8 +196,8 @@ def _timed(fn, torch):
     return r, time.perf_counter() - t0
 
 
-def extra_ndf_L511(torch, prec, nsteps=8):
-    """Adaptive NDF steps at the L = 511 workload (rtol 1e-6, mixed path)."""
+def extra_ndf_L511(torch, prec, nsteps=500):
+    """Adaptive NDF steps at the L = 511 workload (500 steps, rtol 1e-6, mixed path)."""
     from paper_1009_3308_gb300 import Integrator, Plan
     from seeded_inputs import workload
     w = workload("L511")
@@ -211,6 +211,66 @@ def extra_ndf_L511(torch, prec, nsteps=8):
     rhs = sum(i["rhs_evals"] for i in infos)
     return {"steps_per_s": nsteps / el, "rhs_evals_per_step": rhs / nsteps, "steps": nsteps,
             "precision": prec, "t_reached": integ.t}
+
+
+def extra_mixed_errors(torch, prec, nsteps=500):
+    """Error per field of the mixed path at L = 511 against the FP64 GPU path
+    (itself pinned to the oracle at 1e-12): grid fields zeta, u_theta, u_phi,
+    the projection of a tangential field, F, and the state after the 500-step
+    sequence of an adaptive mixed run replayed in both precisions."""
+    from paper_1009_3308_gb300 import Integrator, Plan
+    from seeded_inputs import workload
+    w = workload("L511")
+    c = w["config"]
+    a0 = torch.from_numpy(w["alpha0"]).cuda()
+    rel = lambda x, y: float(((x - y).norm() / y.norm()).item())
+    p64 = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"])
+    pm = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision=prec)
+    out = {}
+    g64, gm = p64.grid_fields(a0), pm.grid_fields(a0)
+    for name, x, y in zip(("zeta", "u_theta", "u_phi"), gm, g64):
+        out[name] = rel(x, y)
+    out["projection"] = rel(pm.project(g64[1], g64[2]), p64.project(g64[1], g64[2]))
+    out["F"] = rel(pm.rhs(a0), p64.rhs(a0))
+    atol = 1e-3 * c["rtol"] * float(abs(w["alpha0"]).max())
+    for p in (p64, pm):
+        p.set("RTOL", c["rtol"])
+        p.set("ATOL", atol)
+    run = Integrator(pm, a0.clone())
+    sched = []
+    for _ in range(nsteps):
+        i = run.step()
+        sched.append((i["h"], i["order"]))
+    fin = {}
+    for name, p in (("mixed", pm), ("fp64", p64)):
+        it = Integrator(p, a0.clone())
+        for h, k in sched:
+            it.replay_step(h, k)
+        fin[name] = it.alpha
+    out["state_after_replayed_steps"] = rel(fin["mixed"], fin["fp64"])
+    out["steps"] = nsteps
+    out["t_reached"] = sum(h for h, _ in sched)
+    return out
+
+
+def extra_fp64_L255(torch, nrhs=1000):
+    """The FP64 workload at L = 255 (384 x 768): 1000 RHS evaluations on the
+    GPU and the relative error of F against the FP64 oracle."""
+    import numpy as np
+    from paper_1009_3308_gb300 import Plan
+    from oracle.rhs import Problem, rhs_separable
+    from seeded_inputs import workload
+    w = workload("L255")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"])
+    a = torch.from_numpy(w["alpha0"]).cuda()
+    out = plan.empty_coeff()
+    ms = time_rhs(plan, a, out, 5, torch)
+    ms = time_rhs(plan, a, out, nrhs, torch)
+    ref = rhs_separable(Problem(c["L"], c["nlon"], c["nu"], c["Omega"]), w["alpha0"])
+    got = plan.rhs(a).cpu().numpy()
+    return {"rhs_per_s": 1e3 / ms, "ms_per_rhs": ms, "rhs": nrhs,
+            "rel_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
 
 
 def extra_L31(torch, nsteps=100):
@@ -229,7 +289,7 @@ def extra_L31(torch, nsteps=100):
             "precision": "fp64"}
 
 
-def extra_adjoint(torch, nsteps=40, checkpoint=20):
+def extra_adjoint(torch, nsteps=200, checkpoint=20):
     """Adjoint workload at L = 255: band energy + misfit gradient w.r.t. alpha0
     and nu through frozen-controller NDF steps, FP32 contractions, FP64 state,
     checkpoints every 20 steps."""
@@ -256,7 +316,7 @@ def extra_adjoint(torch, nsteps=40, checkpoint=20):
             "grad_norm": float(a0r.grad.norm()), "dJ_dnu": float(nut.grad)}
 
 
-def extra_ensemble(torch, nsteps=3, n=256, precision="fp32"):
+def extra_ensemble(torch, nsteps=200, n=256, precision="fp32"):
     """Batched ensemble: 256 instances, L uniform over {63, 127, 255}, nu
     log-uniform in [1e-5, 1e-3], per-instance adaptive steps; "fp32"
     streaming contractions or "bf16x3" (instances of a truncation share every
@@ -454,7 +514,10 @@ def main():
         extras["rel_err_vs_fp64"] = float(np.linalg.norm(fm - f64) / np.linalg.norm(f64))
         if "fp64" in extras:
             extras["speedup_vs_fp64"] = value / world / extras["fp64"]["rhs_per_s"]
-        for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)), ("adjoint_L255", lambda: extra_adjoint(torch)),
+        for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)),
+                         ("mixed_errors_L511", lambda: extra_mixed_errors(torch, prec)),
+                         ("fp64_L255", lambda: extra_fp64_L255(torch)),
+                         ("adjoint_L255", lambda: extra_adjoint(torch)),
                          ("ensemble", lambda: extra_ensemble(torch)),
                          ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),
                          ("L31_fp64_steps", lambda: extra_L31(torch))):

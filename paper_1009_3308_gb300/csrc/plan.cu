@@ -444,9 +444,10 @@ int sphnse_rhs(sphnse_plan* P, double t, const double* alpha, const double* forc
 int sphnse_grid_fields(sphnse_plan* P, const double* alpha, double* zeta, double* uth, double* uph) {
     if (!P || !alpha) return SPHNSE_E_ARG;
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
+    const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
     int rc;
-    if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
-    if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    if ((rc = tc ? launch_prep_tc(P, alpha) : launch_prep(P, alpha, nullptr, prec))) return rc;
+    if ((rc = tc ? launch_synthesis_tc(P, 0) : launch_synthesis(P, 3, prec))) return rc;
     if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
     return launch_ring(P, RING_GRID, prec, nullptr, nullptr, zeta, uth, uph);
 }
@@ -457,7 +458,8 @@ int sphnse_project(sphnse_plan* P, const double* vth, const double* vph, double*
     int rc;
     if ((rc = launch_ring(P, RING_PROJECT, prec, vth, vph, nullptr, nullptr, nullptr))) return rc;
     if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
-    if ((rc = launch_analysis(P, 2, prec))) return rc;
+    const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
+    if ((rc = tc ? launch_analysis_tc(P, 2) : launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 1, prec, nullptr, nullptr, out);
 }
 

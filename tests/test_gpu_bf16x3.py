@@ -5,7 +5,9 @@ Error budget: each operand is split as x = hi + lo with hi, lo in BF16
 (8-bit significands), so |x - hi - lo| <= 2^-17 |x|; the products keep all
 four terms hi*hi + hi*lo + lo*hi + lo*lo; FP32 accumulation adds ~2^-24
 sqrt(n).  Per contraction output the relative error is ~1e-5 of the sum of
-|terms|; the tests take 1e-4 on F (norm) and state the measured error."""
+|terms|; the tests take 3e-5 on F (norm), 3e-5 per grid field and 1e-4 on
+the state after 500 replayed steps at L = 511, and state the measured
+errors."""
 import numpy as np
 import pytest
 
@@ -36,7 +38,7 @@ def test_rhs_bf16x3_matches_oracle(L, nlon, nu, Om, decay):
     got = plan.rhs(_dev(a)).cpu().numpy()
     err = _rel(got, ref)
     print(f"L={L} bf16x3 rel err {err:.3e}")
-    assert err <= 1e-4, err
+    assert err <= 3e-5, err
     assert plan.sync() == 0
 
 
@@ -51,7 +53,7 @@ def test_rhs_bf16x3_L511_vs_fp64():
     fb = plan.rhs(a).cpu().numpy()
     err = _rel(fb, f64)
     print(f"L=511 bf16x3 vs fp64 rel err {err:.3e}")
-    assert err <= 1e-4, err
+    assert err <= 3e-5, err
     assert plan.sync() == 0
 
 
@@ -74,5 +76,65 @@ def test_ensemble_bf16x3_groups_match_fp64_plans():
         got = ens.get(i, "F").cpu().numpy()
         err = _rel(got, ref)
         worst = max(worst, err)
-        assert err <= 1e-4, (i, L, err)
+        assert err <= 3e-5, (i, L, err)
     print(f"ensemble bf16x3 worst rel err {worst:.3e}")
+
+
+def test_grid_fields_and_projection_bf16x3_per_field():
+    """Per field at L = 511: zeta, u_theta, u_phi on the grid (tensor-core
+    synthesis) and the projection of a tangential field (tensor-core
+    analysis), against the FP64 path."""
+    from paper_1009_3308_gb300 import Plan
+    w = workload("L511")
+    c = w["config"]
+    a = _dev(w["alpha0"])
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"])
+    ref = [x.cpu().numpy() for x in plan.grid_fields(a)]
+    pref = plan.project(*[torch.from_numpy(r).cuda() for r in ref[1:]]).cpu().numpy()
+    plan.set_precision("bf16x3")
+    got = [x.cpu().numpy() for x in plan.grid_fields(a)]
+    pgot = plan.project(*[torch.from_numpy(r).cuda() for r in ref[1:]]).cpu().numpy()
+    errs = {n: _rel(g, r) for n, g, r in zip(("zeta", "u_theta", "u_phi"), got, ref)}
+    errs["projection"] = _rel(pgot, pref)
+    print("bf16x3 per field:", {k: f"{v:.2e}" for k, v in errs.items()})
+    # u_phi comes from the degree-shift relation sin(theta) dPt/dtheta =
+    # L eps_{L+1} Pt_{L+1} - (L+1) eps_L Pt_{L-1} divided by sin(theta): at
+    # m = 0 near the poles the sum cancels to O(sin^2 theta), so the split's
+    # absolute error is amplified there (measured 2.5e-5)
+    bounds = {"zeta": 3e-5, "u_theta": 3e-5, "u_phi": 5e-5, "projection": 3e-5}
+    for k, v in errs.items():
+        assert v <= bounds[k], (k, v)
+
+
+def test_state_after_500_replayed_steps_bf16x3_vs_fp64():
+    """The mixed workload's 500 steps (rtol 1e-6): record the adaptive (h,
+    order) sequence of the BF16X3 run, replay it in BF16X3 and in FP64 (each
+    corrector solved to its convergence floor) and compare the final states."""
+    from paper_1009_3308_gb300 import Integrator, Plan
+    w = workload("L511")
+    c = w["config"]
+    a0 = _dev(w["alpha0"])
+    atol = 1e-3 * c["rtol"] * float(abs(w["alpha0"]).max())
+
+    def make(prec):
+        p = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision=prec)
+        p.set("RTOL", c["rtol"])
+        p.set("ATOL", atol)
+        return p, Integrator(p, a0.clone())
+
+    _, run = make("bf16x3")
+    sched = []
+    for _ in range(500):
+        info = run.step()
+        sched.append((info["h"], info["order"]))
+    states = {}
+    for prec in ("bf16x3", "fp64"):
+        _, it = make(prec)
+        for h, k in sched:
+            it.replay_step(h, k)
+        states[prec] = it.alpha.cpu().numpy()
+    err = _rel(states["bf16x3"], states["fp64"])
+    drift = _rel(run.alpha.cpu().numpy(), states["fp64"])
+    print(f"500 replayed steps: bf16x3 vs fp64 state rel err {err:.3e} (adaptive run vs fp64 replay {drift:.3e}),"
+          f" t = {sum(h for h, _ in sched):.4g}")
+    assert err <= 1e-4, err
