@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace sph {
 namespace {
@@ -46,14 +47,6 @@ struct InstPar {
     double h0;     // initial step (init kernel)
 };
 
-__device__ __forceinline__ void amax8(unsigned long long* slots, int idx, double v) {
-    if (!(v <= 1.0e300)) {
-        atomicMax(slots + 7, 1ull);
-        return;
-    }
-    atomicMax(slots + idx, static_cast<unsigned long long>(__double_as_longlong(v)));
-}
-
 #define INST_PROLOGUE                                        \
     const InstPar& p = par[blockIdx.y];                      \
     if (!p.active) return;                                   \
@@ -61,11 +54,22 @@ __device__ __forceinline__ void amax8(unsigned long long* slots, int idx, double
     if (i >= p.n) return;                                    \
     const long o = p.off;
 
+// the norm kernels keep every thread of an active block to the end (block reduction)
+#define INST_PROLOGUE_ALL                                    \
+    const InstPar& p = par[blockIdx.y];                      \
+    if (!p.active) return;                                   \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;     \
+    const long o = p.off;
+
 __global__ void kb_wnorm(const InstPar* par, const double2* v, const double2* y, unsigned long long* norms, int slot) {
-    INST_PROLOGUE
-    const double2 a = v[o + i], b = y[o + i];
-    const double r = fmax(fabs(a.x) / fmax(fabs(b.x), p.thr), fabs(a.y) / fmax(fabs(b.y), p.thr));
-    amax8(norms + 8 * blockIdx.y, slot, r);
+    INST_PROLOGUE_ALL
+    double r[1] = {0.0};
+    if (i < p.n) {
+        const double2 a = v[o + i], b = y[o + i];
+        r[0] = fmax(fabs(a.x) / fmax(fabs(b.x), p.thr), fabs(a.y) / fmax(fabs(b.y), p.thr));
+    }
+    const int id[1] = {slot};
+    block_amax<1>(norms + 8 * blockIdx.y, r, id);
 }
 
 __global__ void kb_init(const InstPar* par, double2* dif, const double2* F) {
@@ -114,31 +118,35 @@ __global__ void kb_predict(const InstPar* par, const double2* y, const double2* 
 __global__ void kb_newton(const InstPar* par, const double2* F, const double2* y, const double2* y0,
                           const double2* psi, double2* d, double2* ynew, const double2* dif,
                           unsigned long long* norms) {
-    INST_PROLOGUE
-    const int L = p.lm[i].x, m = p.lm[i].y;
-    const double lam = double(L) * (L + 1.0);
-    const double mr = 1.0 + p.c * p.nu * lam, mi = -p.c * 2.0 * p.Omega * m / lam;
-    const double2 f = F[o + i], ps = psi[o + i], dd = d[o + i], yo = y[o + i], yn = ynew[o + i], a0 = y0[o + i];
-    const double rx = p.c * f.x - (ps.x + dd.x), ry = p.c * f.y - (ps.y + dd.y);
-    const double den = mr * mr + mi * mi;
-    const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
-    const double thr = p.thr;
-    const double wx = fmax(fmax(fabs(yo.x), fabs(yn.x)), thr), wy = fmax(fmax(fabs(yo.y), fabs(yn.y)), thr);
-    unsigned long long* nm = norms + 8 * blockIdx.y;
-    amax8(nm, 0, fmax(fabs(dlx) / wx, fabs(dly) / wy));
-    const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
-    const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
-    d[o + i] = dn;
-    ynew[o + i] = yv;
-    const double vx = fmax(fmax(fabs(yo.x), fabs(yv.x)), thr), vy = fmax(fmax(fabs(yo.y), fabs(yv.y)), thr);
-    amax8(nm, 1, fmax(fabs(dn.x) / vx, fabs(dn.y) / vy));
-    const double2* D = dif + 7 * o;
-    if (p.k >= 2) {
-        const double2 q = D[size_t(p.k - 1) * p.n + i];
-        amax8(nm, 2, fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy));
+    INST_PROLOGUE_ALL
+    double nv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < p.n) {
+        const int L = p.lm[i].x, m = p.lm[i].y;
+        const double lam = double(L) * (L + 1.0);
+        const double mr = 1.0 + p.c * p.nu * lam, mi = -p.c * 2.0 * p.Omega * m / lam;
+        const double2 f = F[o + i], ps = psi[o + i], dd = d[o + i], yo = y[o + i], yn = ynew[o + i], a0 = y0[o + i];
+        const double rx = p.c * f.x - (ps.x + dd.x), ry = p.c * f.y - (ps.y + dd.y);
+        const double den = mr * mr + mi * mi;
+        const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
+        const double thr = p.thr;
+        const double wx = fmax(fmax(fabs(yo.x), fabs(yn.x)), thr), wy = fmax(fmax(fabs(yo.y), fabs(yn.y)), thr);
+        nv[0] = fmax(fabs(dlx) / wx, fabs(dly) / wy);
+        const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
+        const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
+        d[o + i] = dn;
+        ynew[o + i] = yv;
+        const double vx = fmax(fmax(fabs(yo.x), fabs(yv.x)), thr), vy = fmax(fmax(fabs(yo.y), fabs(yv.y)), thr);
+        nv[1] = fmax(fabs(dn.x) / vx, fabs(dn.y) / vy);
+        const double2* D = dif + 7 * o;
+        if (p.k >= 2) {
+            const double2 q = D[size_t(p.k - 1) * p.n + i];
+            nv[2] = fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy);
+        }
+        const double2 r2 = D[size_t(p.k) * p.n + i];
+        nv[3] = fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy);
     }
-    const double2 r2 = D[size_t(p.k) * p.n + i];
-    amax8(nm, 3, fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy));
+    const int id[4] = {0, 1, 2, 3};
+    block_amax<4>(norms + 8 * blockIdx.y, nv, id);
 }
 
 __global__ void kb_accept(const InstPar* par, double2* dif, const double2* d, double2* y, const double2* ynew) {

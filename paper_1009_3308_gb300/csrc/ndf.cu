@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace sph {
 
@@ -80,16 +81,6 @@ inline double d2u_max(unsigned long long v) {
 // ---------------------------------------------------------------------------
 // device kernels (one thread per packed complex entry)
 
-// slots[idx] = max(slots[idx], v): non-negative doubles order like their bit
-// patterns; a non-finite v is reported in slots[7] instead
-__device__ __forceinline__ void amax(unsigned long long* slots, int idx, double v) {
-    if (!(v <= 1.0e300)) {
-        atomicMax(slots + 7, 1ull);
-        return;
-    }
-    atomicMax(slots + idx, static_cast<unsigned long long>(__double_as_longlong(v)));
-}
-
 __device__ __forceinline__ double wmax(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
 __global__ void k_zero_dif(double2* dif, const double2* F, double h, int n) {
@@ -103,10 +94,13 @@ __global__ void k_zero_dif(double2* dif, const double2* F, double h, int n) {
 // ||v / max(|y|, thr)||_inf into slot
 __global__ void k_wnorm(const double2* v, const double2* y, double thr, unsigned long long* slots, int idx, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double2 a = v[i], b = y[i];
-    const double r = fmax(fabs(a.x) / fmax(fabs(b.x), thr), fabs(a.y) / fmax(fabs(b.y), thr));
-    amax(slots, idx, r);
+    double r[1] = {0.0};
+    if (i < n) {
+        const double2 a = v[i], b = y[i];
+        r[0] = fmax(fabs(a.x) / fmax(fabs(b.x), thr), fabs(a.y) / fmax(fabs(b.y), thr));
+    }
+    const int id[1] = {idx};
+    block_amax<1>(slots, r, id);
 }
 
 __global__ void k_rescale(double2* dif, Mat A, int k, int n) {
@@ -152,29 +146,33 @@ __global__ void k_newton(const double2* F, const double2* y, const double2* y0, 
                          double2* ynew, const double2* dkm1, const double2* dk, const int2* lm, double c,
                          double nu, double Omega, double thr, unsigned long long* slot, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int L = lm[i].x, m = lm[i].y;
-    const double lam = double(L) * (L + 1.0);
-    // 1 - c J_d = (1 + c nu lam) - i c 2 Omega m / lam
-    const double mr = 1.0 + c * nu * lam, mi = -c * 2.0 * Omega * m / lam;
-    const double2 f = F[i], ps = psi[i], dd = d[i], yo = y[i], yn = ynew[i], a0 = y0[i];
-    const double rx = c * f.x - (ps.x + dd.x), ry = c * f.y - (ps.y + dd.y);
-    const double den = mr * mr + mi * mi;
-    const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
-    const double wx = wmax(fabs(yo.x), fabs(yn.x), thr), wy = wmax(fabs(yo.y), fabs(yn.y), thr);
-    amax(slot, 0, fmax(fabs(dlx) / wx, fabs(dly) / wy));
-    const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
-    const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
-    d[i] = dn;
-    ynew[i] = yv;
-    const double vx = wmax(fabs(yo.x), fabs(yv.x), thr), vy = wmax(fabs(yo.y), fabs(yv.y), thr);
-    amax(slot, 1, fmax(fabs(dn.x) / vx, fabs(dn.y) / vy));
-    if (dkm1) {
-        const double2 q = dkm1[i];
-        amax(slot, 2, fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy));
+    double nv[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        const int L = lm[i].x, m = lm[i].y;
+        const double lam = double(L) * (L + 1.0);
+        // 1 - c J_d = (1 + c nu lam) - i c 2 Omega m / lam
+        const double mr = 1.0 + c * nu * lam, mi = -c * 2.0 * Omega * m / lam;
+        const double2 f = F[i], ps = psi[i], dd = d[i], yo = y[i], yn = ynew[i], a0 = y0[i];
+        const double rx = c * f.x - (ps.x + dd.x), ry = c * f.y - (ps.y + dd.y);
+        const double den = mr * mr + mi * mi;
+        const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
+        const double wx = wmax(fabs(yo.x), fabs(yn.x), thr), wy = wmax(fabs(yo.y), fabs(yn.y), thr);
+        nv[0] = fmax(fabs(dlx) / wx, fabs(dly) / wy);
+        const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
+        const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
+        d[i] = dn;
+        ynew[i] = yv;
+        const double vx = wmax(fabs(yo.x), fabs(yv.x), thr), vy = wmax(fabs(yo.y), fabs(yv.y), thr);
+        nv[1] = fmax(fabs(dn.x) / vx, fabs(dn.y) / vy);
+        if (dkm1) {
+            const double2 q = dkm1[i];
+            nv[2] = fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy);
+        }
+        const double2 r2 = dk[i];
+        nv[3] = fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy);
     }
-    const double2 r2 = dk[i];
-    amax(slot, 3, fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy));
+    const int id[4] = {0, 1, 2, 3};
+    block_amax<4>(slot, nv, id);
 }
 
 // D_{k+1} = d - D_k; D_k = d; D_j += D_{j+1} (j = k-1..0); y = ynew
@@ -221,27 +219,31 @@ __global__ void k_adj_accept(double2* dbar, const double2* abar, double2* dtot, 
 __global__ void k_adj_fixpoint(double2* mu, const double2* b, const double2* JT, const int2* lm, double c,
                                double nu, double Omega, unsigned long long* slot, int first, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int L = lm[i].x, m = lm[i].y;
-    const double lam = double(L) * (L + 1.0);
-    const double mr = 1.0 + c * nu * lam, mi = c * 2.0 * Omega * m / lam;  // conj(1 - c J_d)
-    const double2 bb = b[i];
-    double rx, ry;
-    double2 u = make_double2(0.0, 0.0);
-    if (first) {
-        rx = bb.x;
-        ry = bb.y;
-    } else {
-        u = mu[i];
-        const double2 jt = JT[i];
-        rx = bb.x - u.x + c * jt.x;
-        ry = bb.y - u.y + c * jt.y;
+    double r[1] = {0.0};
+    if (i < n) {
+        const int L = lm[i].x, m = lm[i].y;
+        const double lam = double(L) * (L + 1.0);
+        const double mr = 1.0 + c * nu * lam, mi = c * 2.0 * Omega * m / lam;  // conj(1 - c J_d)
+        const double2 bb = b[i];
+        double rx, ry;
+        double2 u = make_double2(0.0, 0.0);
+        if (first) {
+            rx = bb.x;
+            ry = bb.y;
+        } else {
+            u = mu[i];
+            const double2 jt = JT[i];
+            rx = bb.x - u.x + c * jt.x;
+            ry = bb.y - u.y + c * jt.y;
+        }
+        r[0] = fmax(fabs(rx), fabs(ry));
+        const double den = mr * mr + mi * mi;
+        u.x += (rx * mr + ry * mi) / den;
+        u.y += (ry * mr - rx * mi) / den;
+        mu[i] = u;
     }
-    amax(slot, 0, fmax(fabs(rx), fabs(ry)));
-    const double den = mr * mr + mi * mi;
-    u.x += (rx * mr + ry * mi) / den;
-    u.y += (ry * mr - rx * mi) / den;
-    mu[i] = u;
+    const int id[1] = {0};
+    block_amax<1>(slot, r, id);
 }
 
 // y0bar = abar + mu - dtot;  dbar_j += g_j (-mu) + y0bar (j < k);  abar = y0bar;
@@ -394,8 +396,10 @@ Work work(sphnse_plan* P) {
 
 inline dim3 grid(int n) { return dim3((n + 255) / 256); }
 
+// the eight norm slots through the plan's pinned mirror (a pageable
+// destination would be staged by the driver)
 int read_norms(sphnse_plan* P, double* out, int cnt) {
-    unsigned long long h[8];
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(P->h_norms);
     if (cudaMemcpyAsync(h, P->d_norms, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, P->stream) !=
         cudaSuccess)
         return SPHNSE_E_CUDA;
