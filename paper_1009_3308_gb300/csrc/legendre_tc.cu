@@ -507,6 +507,7 @@ struct TcSynArgs {
     int N, nh, nlat, nblk, pairs;
     int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
     size_t sgs;
+    int m0phi;                   // u_phi at m = 0 from columns 12..15 of the order-1 item (k_prep_tc)
 };
 
 constexpr int TC_SYN_MAXNS = 8;
@@ -664,8 +665,23 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 tmem_ld4_nowait(ce + 8, e + 8);
                 tmem_ld8_nowait(co, o);
                 tmem_ld4_nowait(co + 8, o + 8);
+                const bool phi0 = a.m0phi && m == 1;   // uniform over the item
+                uint32_t pe[4], po[4];
+                if (phi0) {
+                    tmem_ld4_nowait(ce + 12, pe);
+                    tmem_ld4_nowait(co + 12, po);
+                }
                 tmem_wait_ld();
                 if (!ok || p >= nh || *abort) continue;
+                if (phi0) {
+                    const float er = __uint_as_float(pe[0]) + __uint_as_float(pe[2]);
+                    const float ei = __uint_as_float(pe[1]) + __uint_as_float(pe[3]);
+                    const float orr = __uint_as_float(po[0]) + __uint_as_float(po[2]);
+                    const float oi = __uint_as_float(po[1]) + __uint_as_float(po[3]);
+                    float2* o0 = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
+                    o0[gsyn_index(a.pairs, 2, 0, p, N, nlat)] = make_float2(er + orr, ei + oi);
+                    if (nlat - 1 - p != p) o0[gsyn_index(a.pairs, 2, 0, nlat - 1 - p, N, nlat)] = make_float2(er - orr, ei - oi);
+                }
                 float E[6], O[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
@@ -680,6 +696,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                     const float sg = hemi == 0 ? 1.f : -1.f;
 #pragma unroll
                     for (int f = 0; f < 3; ++f) {
+                        if (f == 2 && m == 0 && a.m0phi) break;   // written by the order-1 item
                         const float gr = E[2 * f] + sg * O[2 * f];
                         const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
                         float2 ov;
@@ -710,9 +727,17 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
 // the six columns in rows r0 .. r0+5 and the lo parts in rows r0+6 .. r0+11,
 // r0 = 12 (instance mod ng), of its group's tile (rows past the group's
 // instances stay zero).  All of a thread's loads are independent.
+//
+// m0phi (one instance per 16-row tile): the order-1 tiles also carry, in rows
+// 12..15 (hi re, hi im, lo re, lo im), the column -a_{K,0}.  With
+// d/dtheta Pt_K^0 = sqrt(K (K+1)) Pt_K^1 (ladder relation, Condon-Shortley
+// phase), u_phi at m = 0 is -sum_K alpha_{K,0} Pt_K^1: a sum over the
+// order-1 table that needs no division by sin(theta).  The degree-shift form
+// of the m = 0 column cancels to O(sin^2 theta) near the poles, where the
+// split's rounding would be amplified by 1 / sin(theta).
 __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
                                                  unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
-                                                 int ntiles, int N, int n_coeff, int ng, int brows) {
+                                                 int ntiles, int N, int n_coeff, int ng, int brows, int m0phi) {
     pdl_launch();
     pdl_wait();   // alpha may be the predecessor's output
     const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
@@ -755,6 +780,22 @@ __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alp
     for (int c = 0; c < 6; ++c) {
         *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + c, q)) = pack_hi(v[c]);
         *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + 6 + c, q)) = pack_lo(v[c]);
+    }
+    if (m0phi && m == 1) {
+        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N
+        float re[8], im[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int K = K0 + 2 * e;
+            double2 u = make_double2(0.0, 0.0);
+            if (j0 + e < n && K <= N) u = a0[K];
+            re[e] = -float(u.x);
+            im[e] = -float(u.y);
+        }
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(12, q)) = pack_hi(re);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(13, q)) = pack_hi(im);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(14, q)) = pack_lo(re);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(15, q)) = pack_lo(im);
     }
 }
 
@@ -1053,12 +1094,15 @@ void tc_batch_free(TcBatch* B) {
     *B = TcBatch();
 }
 
+// the m = 0 u_phi column fits when every group is one instance in 16 B rows
+static int tc_m0phi(const TcBatch& B) { return B.ng == 1 && B.brows == 16 ? 1 : 0; }
+
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) {
     stage_begin(P, SPHNSE_STAGE_PREP);
     const cudaError_t e = launch_pdl(k_prep_tc, dim3((P->tc.ntiles + 15) / 16, B.nb), dim3(128), 0, P->stream,
                                      reinterpret_cast<const double2*>(alpha), static_cast<const float4*>(P->d_prepc32),
                                      B.btiles, static_cast<const int2*>(P->tc.tile_info), P->tc.ntiles, P->N,
-                                     P->n_coeff, B.ng, B.brows);
+                                     P->n_coeff, B.ng, B.brows, tc_m0phi(B));
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(e);
 }
@@ -1074,7 +1118,7 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
                 P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
-                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2};
+                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2, tc_m0phi(B)};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     const cudaError_t e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
