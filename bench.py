@@ -273,6 +273,27 @@ def extra_fp64_L255(torch, nrhs=1000):
             "rel_err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
 
 
+def extra_coriolis_split(torch, prec):
+    """RHS/s at the L = 511 workload with the Coriolis term applied as its
+    diagonal (no 2 Omega cos(theta) in the grid product), and its relative
+    difference from the unsplit F in the same precision."""
+    import numpy as np
+    from paper_1009_3308_gb300 import Plan
+    from seeded_inputs import workload
+    w = workload("L511")
+    c = w["config"]
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision=prec)
+    a = torch.from_numpy(w["alpha0"]).cuda()
+    full = plan.rhs(a).cpu().numpy()
+    plan.set("CORIOLIS_SPLIT", 1)
+    out = plan.empty_coeff()
+    time_rhs(plan, a, out, 20, torch)
+    ms = time_rhs(plan, a, out, 1000, torch)
+    split = plan.rhs(a).cpu().numpy()
+    return {"rhs_per_s": 1e3 / ms, "ms_per_rhs": ms, "precision": prec,
+            "rel_diff_vs_unsplit": float(np.linalg.norm(split - full) / np.linalg.norm(full))}
+
+
 def extra_L31(torch, nsteps=100):
     """The L = 31 workload: 100 adaptive FP64 steps, rtol 1e-8, steady forcing."""
     from paper_1009_3308_gb300 import Integrator, Plan
@@ -517,6 +538,7 @@ def main():
         for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)),
                          ("mixed_errors_L511", lambda: extra_mixed_errors(torch, prec)),
                          ("fp64_L255", lambda: extra_fp64_L255(torch)),
+                         ("coriolis_split_L511", lambda: extra_coriolis_split(torch, prec)),
                          ("adjoint_L255", lambda: extra_adjoint(torch)),
                          ("ensemble", lambda: extra_ensemble(torch)),
                          ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),

@@ -63,6 +63,13 @@ extern "C" {
 #define SPHNSE_KEY_NEWTON_MAX_ITER 7  /* simplified-Newton iteration cap (default 4) */
 #define SPHNSE_KEY_H_MAX           8  /* largest step size (default 1) */
 #define SPHNSE_KEY_BDF             9  /* 1: kappa = 0 (BDF), 0: NDF (default) */
+#define SPHNSE_KEY_CORIOLIS_SPLIT 10  /* 1: apply the Coriolis term as the diagonal
+                                         (C Z_{L,m}, Z_{L,m}) = -2 i Omega m / lambda_L
+                                         (Sec. 3, Eq. (Coriolis_ZLm)) in the finish
+                                         step and drop 2 Omega cos(theta) from the
+                                         grid product; 0: in the product (default).
+                                         Same F up to rounding; forward RHS only (the
+                                         adjoint always carries it in the product) */
 #define SPHNSE_KEY_N_COEFF       100  /* read-only: n_coeff */
 #define SPHNSE_KEY_L             101  /* read-only: truncation degree */
 #define SPHNSE_KEY_NLAT          102  /* read-only */

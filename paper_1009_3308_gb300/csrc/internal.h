@@ -138,6 +138,7 @@ struct sphnse_plan {
     int precision = SPHNSE_FP64;
     double rtol = 1e-6, atol = 1e-12, h_max = 1.0;
     int max_order = 5, newton_max = 4, bdf = 0;
+    int coriolis_split = 0;      // Coriolis as the diagonal -2 i Omega m / lambda (forward RHS)
     cudaStream_t stream = nullptr;
     int device = 0;
     int n_coeff = 0, n_ext = 0;

@@ -229,14 +229,16 @@ __global__ void __launch_bounds__(128) k_analysis(const T* __restrict__ pana, co
 //             - (L eps_{L+1,m} H^phi_{L+1} - (L+1) eps_{L,m} H^phi_{L-1}) ]
 // with the FP64 coefficients precomputed per entry:
 // c = (lambda^{-1/2}, L eps_{L+1,m} lambda^{-1/2}, (L+1) eps_{L,m} lambda^{-1/2}, lambda).
-// kind 0: out = forcing - nu lambda alpha - N              (Eq. (ode))
+// kind 0: out = forcing - nu lambda alpha - N              (Eq. (ode));
+//         + 2 i omega_d m / lambda alpha, the Coriolis diagonal of
+//         Eq. (Coriolis_ZLm), when the product leaves it out (omega_d = Omega)
 // kind 1: out = N                                          (projection)
 // kind 2: out = -nu lambda w - s_m (N + lambda^{1/2} H^rho_L)  (J^T w; alpha = w)
 template <typename T>
 __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const double2* __restrict__ alpha,
                          const double2* __restrict__ forcing, double2* __restrict__ out,
                          const int2* __restrict__ lm, const double4_32a* __restrict__ finc, int N, double nu,
-                         int n) {
+                         int n, double omega_d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int L = lm[i].x, m = lm[i].y;
@@ -261,6 +263,11 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
         const double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
         r.x = f.x - nu * lam * a.x - nr;
         r.y = f.y - nu * lam * a.y - ni;
+        if (omega_d != 0.0) {
+            const double cor = 2.0 * omega_d * m / lam;
+            r.x -= cor * a.y;
+            r.y += cor * a.x;
+        }
     } else if (kind == 1) {
         r = make_double2(nr, ni);
     } else {
@@ -279,7 +286,7 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
 __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, const double2* __restrict__ alpha,
                            const double2* __restrict__ forcing, double2* __restrict__ out,
                            const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n,
-                           size_t hstride, const double* __restrict__ nu_inst) {
+                           size_t hstride, const double* __restrict__ nu_inst, double omega_d) {
     pdl_launch();
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -316,6 +323,13 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
         const double nl = nu * lam;
         r.x = fma(-nl, a.x, f.x) - double(nr);
         r.y = fma(-nl, a.y, f.y) - double(ni);
+        if (omega_d != 0.0) {
+            // 2 Omega m / lambda from lambda^{-1/2} in FP32 (relative 1e-7, below
+            // the FP32 and BF16x3 paths' own error); FP64 divides are slow here
+            const double cor = double(2.f * float(omega_d) * float(m) * c.x * c.x);
+            r.x = fma(-cor, a.y, r.x);
+            r.y = fma(cor, a.x, r.y);
+        }
     } else if (kind == 1) {
         r = make_double2(double(nr), double(ni));
     } else {
@@ -414,13 +428,14 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
         k_finish<double><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const double*>(P->d_hana), nf,
                                                      reinterpret_cast<const double2*>(alpha),
                                                      reinterpret_cast<const double2*>(forcing),
-                                                     reinterpret_cast<double2*>(out), P->d_lm, P->d_finc, P->N, P->nu, n);
+                                                     reinterpret_cast<double2*>(out), P->d_lm, P->d_finc, P->N, P->nu, n,
+                                                     kind == 0 && P->coriolis_split ? P->Omega : 0.0);
     else
         launch_pdl(k_finish32, grd, blk, 0, P->stream, kind, static_cast<const float*>(P->d_hana), nf,
                    reinterpret_cast<const double2*>(alpha), reinterpret_cast<const double2*>(forcing),
                    reinterpret_cast<double2*>(out), static_cast<const int2*>(P->d_lm),
                    static_cast<const float4*>(P->d_finc32), P->N, P->nu, n, size_t(0),
-                   static_cast<const double*>(nullptr));
+                   static_cast<const double*>(nullptr), kind == 0 && P->coriolis_split ? P->Omega : 0.0);
     stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }
@@ -444,7 +459,7 @@ int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstr
     launch_pdl(k_finish32, grd, blk, 0, P->stream, 0, hana, 2, reinterpret_cast<const double2*>(alpha),
                static_cast<const double2*>(nullptr), reinterpret_cast<double2*>(out),
                static_cast<const int2*>(P->d_lm), static_cast<const float4*>(P->d_finc32), P->N, P->nu, n, hstride,
-               nu_inst);
+               nu_inst, 0.0);
     stage_end(P, SPHNSE_STAGE_FINISH);
     return check_cuda(cudaGetLastError());
 }

@@ -394,6 +394,7 @@ int sphnse_plan_set(sphnse_plan* P, int key, double v) {
         case SPHNSE_KEY_NEWTON_MAX_ITER: if (v < 1 || v > 1000) return SPHNSE_E_ARG; P->newton_max = int(v); return SPHNSE_OK;
         case SPHNSE_KEY_H_MAX: if (v <= 0) return SPHNSE_E_ARG; P->h_max = v; return SPHNSE_OK;
         case SPHNSE_KEY_BDF: P->bdf = v != 0.0; return SPHNSE_OK;
+        case SPHNSE_KEY_CORIOLIS_SPLIT: P->coriolis_split = v != 0.0; return SPHNSE_OK;
         default: return SPHNSE_E_ARG;
     }
 }
@@ -410,6 +411,7 @@ int sphnse_plan_get(const sphnse_plan* P, int key, double* v) {
         case SPHNSE_KEY_NEWTON_MAX_ITER: *v = P->newton_max; break;
         case SPHNSE_KEY_H_MAX: *v = P->h_max; break;
         case SPHNSE_KEY_BDF: *v = P->bdf; break;
+        case SPHNSE_KEY_CORIOLIS_SPLIT: *v = P->coriolis_split; break;
         case SPHNSE_KEY_N_COEFF: *v = P->n_coeff; break;
         case SPHNSE_KEY_L: *v = P->N; break;
         case SPHNSE_KEY_NLAT: *v = P->nlat; break;

@@ -332,7 +332,7 @@ int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const do
     a.M = P->nlon;
     a.nlat = P->nlat;
     a.mode = mode;
-    a.two_omega = 2.0 * P->Omega;
+    a.two_omega = mode == RING_RHS && P->coriolis_split ? 0.0 : 2.0 * P->Omega;
     a.x = P->d_x;
     a.s = P->d_s;
     a.rw = P->d_rw;
@@ -696,7 +696,7 @@ static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float*
     Ring4Args a;
     a.N = P->N;
     a.nlat = P->nlat;
-    a.two_omega = float(2.0 * P->Omega);
+    a.two_omega = P->coriolis_split ? 0.f : float(2.0 * P->Omega);
     a.x = P->d_x;
     a.rw = P->d_rw;
     a.gsyn = reinterpret_cast<const float2*>(gsyn);

@@ -5,7 +5,7 @@ Error budget: each operand is split as x = hi + lo with hi, lo in BF16
 (8-bit significands), so |x - hi - lo| <= 2^-17 |x|; the products keep all
 four terms hi*hi + hi*lo + lo*hi + lo*lo; FP32 accumulation adds ~2^-24
 sqrt(n).  Per contraction output the relative error is ~1e-5 of the sum of
-|terms|; the tests take 3e-5 on F (norm), 3e-5 per grid field and 1e-4 on
+|terms|; the tests take 3e-5 on F (norm), 1e-5 per grid field and 1e-4 on
 the state after 500 replayed steps at L = 511, and state the measured
 errors."""
 import numpy as np

@@ -144,6 +144,18 @@ def test_coriolis_operator_is_diagonal():
             np.testing.assert_allclose(col, expect, atol=1e-14)
 
 
+def test_split_coriolis_equals_full_rhs():
+    """The split variant (Coriolis as its diagonal, Eq. (Coriolis_ZLm), and a
+    product without 2 Omega cos(theta)) gives the same F at a nonlinear
+    state: F_Omega(alpha) = F_0(alpha) + 2 i Omega m / lambda alpha."""
+    N, M = 12, 38
+    a = coefficients(N, 91, 0.2) * 3.0
+    full = rhs_separable(Problem(N, M, 1e-2, 2.3), a)
+    prob0 = Problem(N, M, 1e-2, 0.0)
+    split = rhs_separable(prob0, a) + 2j * 2.3 * prob0.ms / prob0.lam * a
+    np.testing.assert_allclose(split, full, atol=1e-13 * np.abs(full).max())
+
+
 # ---------------------------------------------------------------------------
 # planted mistakes: each must be caught by one of the pins above
 
