@@ -75,6 +75,8 @@ extern "C" {
 #define SPHNSE_KEY_NLAT          102  /* read-only */
 #define SPHNSE_KEY_NLON          103  /* read-only */
 #define SPHNSE_KEY_TABLE_BYTES   104  /* read-only: device bytes of Legendre tables held */
+#define SPHNSE_KEY_ROUNDS        105  /* read-only (ensemble): graph launches (rounds) of the
+                                         last sphnse_ensemble_advance / _step call */
 
 #define SPHNSE_FP64    0  /* FP64 tables and arithmetic throughout */
 #define SPHNSE_FP32    1  /* FP32 tables, contractions, FFTs; FP64 state and update */
@@ -250,6 +252,9 @@ void sphnse_ensemble_destroy(sphnse_ensemble* ens);
 /* SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX (and
  * _PRECISION, FP32 only). */
 int sphnse_ensemble_set(sphnse_ensemble* ens, int key, double value);
+/* Read SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX,
+ * _PRECISION or _ROUNDS into *value. */
+int sphnse_ensemble_get(sphnse_ensemble* ens, int key, double* value);
 int sphnse_ensemble_set_stream(sphnse_ensemble* ens, void* stream);
 
 /* Device pointers (owned by the ensemble) of instance i's packed state alpha
@@ -264,9 +269,19 @@ int sphnse_ensemble_rhs(sphnse_ensemble* ens);
 int sphnse_ensemble_init(sphnse_ensemble* ens, double t0);
 
 /* One accepted step of every instance, each with its own adaptive step size
- * and order (the controller of sphnse_step), advanced in lockstep by attempt
- * and Newton iteration; info: host array of n entries or NULL. */
+ * and order (the controller of sphnse_step); info: host array of n entries
+ * or NULL.  Same as sphnse_ensemble_advance(ens, 1, info). */
 int sphnse_ensemble_step(sphnse_ensemble* ens, sphnse_step_info* info);
+
+/* nsteps >= 0 accepted steps of every instance, each at its own pace: the
+ * instances advance in rounds of one CUDA-graph launch (accept, rescale and
+ * predictor where due, one batched RHS of all instances, one Newton update)
+ * and one host read of their norms, so an instance never waits for another's
+ * rejected attempts or Newton iterations.  Each instance follows exactly the
+ * step/order sequence sphnse_step gives it alone.  info (host, n entries or
+ * NULL): the last step's t, h, err, order, next_order, next_h, h_dif_before,
+ * with newton_iters, rhs_evals and rejections summed over the call. */
+int sphnse_ensemble_advance(sphnse_ensemble* ens, int nsteps, sphnse_step_info* info);
 
 /* ---- stage timing ------------------------------------------------------- */
 

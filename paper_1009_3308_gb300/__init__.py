@@ -238,6 +238,15 @@ class Ensemble:
     def set(self, key, value):
         check("sphnse_ensemble_set", _capi.lib().sphnse_ensemble_set(self._h, KEY[key], float(value)))
 
+    def get(self, key, i=None, field="alpha"):
+        """get("KEY") reads an ensemble parameter (e.g. "ROUNDS"); get(i) /
+        get(i, "F") a copy of instance i's state or last RHS."""
+        if isinstance(key, str):
+            v = ctypes.c_double()
+            check("sphnse_ensemble_get", _capi.lib().sphnse_ensemble_get(self._h, KEY[key], ctypes.byref(v)))
+            return v.value
+        return self._get_instance(key, field if i is None else i)
+
     def _stream(self):
         torch = _torch()
         s = torch.cuda.current_stream(self.device).cuda_stream
@@ -259,7 +268,7 @@ class Ensemble:
         torch.cuda.current_stream(self.device).synchronize()
         _cudart_copy(a, src.data_ptr(), nc * 16)
 
-    def get(self, i, which="alpha"):
+    def _get_instance(self, i, which="alpha"):
         """Copy of instance i's state ('alpha') or last RHS ('F')."""
         torch = _torch()
         a, f, nc = self._ptrs(i)
@@ -280,6 +289,16 @@ class Ensemble:
         infos = (StepInfo * self.n)()
         self._stream()
         check("sphnse_ensemble_step", _capi.lib().sphnse_ensemble_step(self._h, ctypes.cast(infos, ctypes.c_void_p)))
+        return [x.as_dict() for x in infos]
+
+    def advance(self, nsteps):
+        """nsteps accepted steps of every instance, each at its own pace
+        (asynchronous rounds); per instance the info of its last step, with
+        Newton iterations, RHS evaluations and rejections summed over the call."""
+        infos = (StepInfo * self.n)()
+        self._stream()
+        check("sphnse_ensemble_advance", _capi.lib().sphnse_ensemble_advance(
+            self._h, int(nsteps), ctypes.cast(infos, ctypes.c_void_p)))
         return [x.as_dict() for x in infos]
 
 

@@ -11,10 +11,14 @@
 //
 // Time stepping: every instance keeps its own adaptive NDF controller (step
 // size, order, Newton rate; the same quasi-constant step-size scheme as
-// sphnse_step, Sec. 4.2 Eq. (ode_disc)).  The controllers run in lockstep by
-// attempt and Newton iteration: per-instance parameters live in a device
-// array read by the batched kernels, inactive instances are masked, and the
-// host reads all instances' norms once per Newton iteration.
+// sphnse_step, Sec. 4.2 Eq. (ode_disc)).  The instances advance
+// asynchronously in rounds: one round is one captured graph -- accept of the
+// previous step, rescale and predictor of a new attempt, one batched RHS and
+// one Newton update -- in which every instance does whatever its own
+// controller is at (flag bits in a per-instance parameter array), followed by
+// one read of all instances' norms.  An instance that converges, rejects or
+// accepts starts its next attempt in the next round, so no instance waits for
+// another's rejected attempts or extra Newton iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +29,8 @@
 #include <vector>
 
 #include "internal.h"
+#include "dmath.cuh"
+#include "newton.cuh"
 #include "reduce.cuh"
 
 namespace sph {
@@ -33,12 +39,19 @@ namespace {
 constexpr double EPS = 2.220446049250313e-16;
 const double KAPPA_E[SPHNSE_MAXK] = {-0.1850, -1.0 / 9.0, -0.0823, -0.0415, 0.0};
 
+// flag bits of InstPar::flags: what an instance does in the current launch
+constexpr int F_INIT = 1;       // initial weight norm of F and zeroed differences
+constexpr int F_ACCEPT = 2;     // apply the step accepted in the previous round (order ka)
+constexpr int F_RESCALE = 4;    // rescale the differences to a new step size
+constexpr int F_PREDICT = 8;    // predictor of a new attempt (and the weight norm of alpha)
+constexpr int F_NEWTON = 16;    // one simplified-Newton update at the batched RHS
+
 struct InstPar {
     long off;      // offset (complex entries) of this instance in the concatenated vectors
     int n;         // packed entries
     int k;         // order of the current attempt
-    int active;    // participates in the current launch
-    int rescale;   // rescale the differences in this attempt
+    int flags;     // F_* bits for the current launch
+    int ka;        // order of the step accepted by F_ACCEPT
     double c;      // h * iga_k
     double nu, Omega, thr;
     const int2* lm;
@@ -47,42 +60,44 @@ struct InstPar {
     double h0;     // initial step (init kernel)
 };
 
-#define INST_PROLOGUE                                        \
-    const InstPar& p = par[blockIdx.y];                      \
-    if (!p.active) return;                                   \
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;     \
-    if (i >= p.n) return;                                    \
+// One 256-thread block per (instance, 256 consecutive entries): the block
+// table btab lists (instance, block of the instance), so no block is empty
+// and a block never spans two instances (the norm reductions are per block).
+constexpr int EB = 256;
+
+#define INST_PROLOGUE_ALL(FLAG)                              \
+    const int2 bt = btab[blockIdx.x];                        \
+    const InstPar& p = par[bt.x];                            \
+    if (!(p.flags & (FLAG))) return;                         \
+    const int i = bt.y * EB + threadIdx.x;                   \
     const long o = p.off;
 
-// the norm kernels keep every thread of an active block to the end (block reduction)
-#define INST_PROLOGUE_ALL                                    \
-    const InstPar& p = par[blockIdx.y];                      \
-    if (!p.active) return;                                   \
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;     \
-    const long o = p.off;
+#define INST_PROLOGUE(FLAG)                                  \
+    INST_PROLOGUE_ALL(FLAG)                                  \
+    if (i >= p.n) return;
 
-__global__ void kb_wnorm(const InstPar* par, const double2* v, const double2* y, unsigned long long* norms, int slot) {
-    INST_PROLOGUE_ALL
+__global__ void kb_wnorm(const int2* btab, const InstPar* par, int flag, const double2* v, const double2* y,
+                         unsigned long long* norms, int slot) {
+    INST_PROLOGUE_ALL(flag)
     double r[1] = {0.0};
     if (i < p.n) {
         const double2 a = v[o + i], b = y[o + i];
-        r[0] = fmax(fabs(a.x) / fmax(fabs(b.x), p.thr), fabs(a.y) / fmax(fabs(b.y), p.thr));
+        r[0] = fmax(fabs(a.x) * rcp64<1>(fmax(fabs(b.x), p.thr)), fabs(a.y) * rcp64<1>(fmax(fabs(b.y), p.thr)));
     }
     const int id[1] = {slot};
-    block_amax<1>(norms + 8 * blockIdx.y, r, id);
+    block_amax<1>(norms + 8 * bt.x, r, id);
 }
 
-__global__ void kb_init(const InstPar* par, double2* dif, const double2* F) {
-    INST_PROLOGUE
+__global__ void kb_init(const int2* btab, const InstPar* par, double2* dif, const double2* F) {
+    INST_PROLOGUE(F_INIT)
     const double2 f = F[o + i];
     double2* D = dif + 7 * o;
     D[i] = make_double2(p.h0 * f.x, p.h0 * f.y);
     for (int j = 1; j < SPHNSE_MAXK + 2; ++j) D[size_t(j) * p.n + i] = make_double2(0.0, 0.0);
 }
 
-__global__ void kb_rescale(const InstPar* par, double2* dif) {
-    INST_PROLOGUE
-    if (!p.rescale) return;
+__global__ void kb_rescale(const int2* btab, const InstPar* par, double2* dif) {
+    INST_PROLOGUE(F_RESCALE)
     double2* D = dif + 7 * o;
     double2 old[SPHNSE_MAXK];
     for (int j = 0; j < p.k; ++j) old[j] = D[size_t(j) * p.n + i];
@@ -97,9 +112,9 @@ __global__ void kb_rescale(const InstPar* par, double2* dif) {
     }
 }
 
-__global__ void kb_predict(const InstPar* par, const double2* y, const double2* dif, double2* y0, double2* psi,
-                           double2* d, double2* ynew) {
-    INST_PROLOGUE
+__global__ void kb_predict(const int2* btab, const InstPar* par, const double2* y, const double2* dif, double2* y0,
+                           double2* psi, double2* d, double2* ynew) {
+    INST_PROLOGUE(F_PREDICT)
     const double2* D = dif + 7 * o;
     double2 a = y[o + i], q = make_double2(0.0, 0.0);
     for (int j = 0; j < p.k; ++j) {
@@ -115,44 +130,33 @@ __global__ void kb_predict(const InstPar* par, const double2* y, const double2* 
     d[o + i] = make_double2(0.0, 0.0);
 }
 
-__global__ void kb_newton(const InstPar* par, const double2* F, const double2* y, const double2* y0,
-                          const double2* psi, double2* d, double2* ynew, const double2* dif,
+__global__ void kb_newton(const int2* btab, const InstPar* par, const double2* F, const double2* y,
+                          const double2* y0, const double2* psi, double2* d, double2* ynew, const double2* dif,
                           unsigned long long* norms) {
-    INST_PROLOGUE_ALL
-    double nv[4] = {0.0, 0.0, 0.0, 0.0};
+    INST_PROLOGUE_ALL(F_NEWTON)
+    float nv[4] = {0.f, 0.f, 0.f, 0.f};
+    bool bad = false;
     if (i < p.n) {
-        const int L = p.lm[i].x, m = p.lm[i].y;
-        const double lam = double(L) * (L + 1.0);
-        const double mr = 1.0 + p.c * p.nu * lam, mi = -p.c * 2.0 * p.Omega * m / lam;
-        const double2 f = F[o + i], ps = psi[o + i], dd = d[o + i], yo = y[o + i], yn = ynew[o + i], a0 = y0[o + i];
-        const double rx = p.c * f.x - (ps.x + dd.x), ry = p.c * f.y - (ps.y + dd.y);
-        const double den = mr * mr + mi * mi;
-        const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
-        const double thr = p.thr;
-        const double wx = fmax(fmax(fabs(yo.x), fabs(yn.x)), thr), wy = fmax(fmax(fabs(yo.y), fabs(yn.y)), thr);
-        nv[0] = fmax(fabs(dlx) / wx, fabs(dly) / wy);
-        const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
-        const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
-        d[o + i] = dn;
-        ynew[o + i] = yv;
-        const double vx = fmax(fmax(fabs(yo.x), fabs(yv.x)), thr), vy = fmax(fmax(fabs(yo.y), fabs(yv.y)), thr);
-        nv[1] = fmax(fabs(dn.x) / vx, fabs(dn.y) / vy);
+        const int2 q = p.lm[i];
         const double2* D = dif + 7 * o;
-        if (p.k >= 2) {
-            const double2 q = D[size_t(p.k - 1) * p.n + i];
-            nv[2] = fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy);
-        }
-        const double2 r2 = D[size_t(p.k) * p.n + i];
-        nv[3] = fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy);
+        const NewtonEntry e = newton_entry(q.x, q.y, p.c, float(p.nu), float(2.0 * p.Omega), fmaxf(float(p.thr), 1e-30f),
+                                           F[o + i], psi[o + i], d[o + i], y[o + i], ynew[o + i], y0[o + i],
+                                           p.k >= 2 ? D + size_t(p.k - 1) * p.n + i : nullptr,
+                                           D[size_t(p.k) * p.n + i]);
+        d[o + i] = e.dn;
+        ynew[o + i] = e.yv;
+        for (int j = 0; j < 4; ++j) nv[j] = e.nv[j];
+        bad = e.bad;
     }
     const int id[4] = {0, 1, 2, 3};
-    block_amax<4>(norms + 8 * blockIdx.y, nv, id);
+    block_amax_f<4>(norms + 8 * bt.x, nv, id, bad);
 }
 
-__global__ void kb_accept(const InstPar* par, double2* dif, const double2* d, double2* y, const double2* ynew) {
-    INST_PROLOGUE
+__global__ void kb_accept(const int2* btab, const InstPar* par, double2* dif, const double2* d, double2* y,
+                          const double2* ynew) {
+    INST_PROLOGUE(F_ACCEPT)
     double2* D = dif + 7 * o;
-    const int k = p.k;
+    const int k = p.ka;
     const double2 dd = d[o + i], dk = D[size_t(k) * p.n + i];
     D[size_t(k + 1) * p.n + i] = make_double2(dd.x - dk.x, dd.y - dk.y);
     double2 up = dd;
@@ -200,7 +204,15 @@ struct Ctl {
     bool attempting = false, in_newton = false, conv = false;
     int its = 0;
     double oldnrm = 0, ynorm = 0, nrm[4] = {0, 0, 0, 0};
+    // asynchronous rounds
+    int state = 0;                // S_IDLE, S_START (new attempt next round), S_NEWTON
+    int it = 0;                   // Newton iteration of the current attempt
+    int steps_left = 0, attempts = 0;
+    bool pending_accept = false;  // F_ACCEPT in the next launch
+    int acc_k = 1;
 };
+
+constexpr int S_IDLE = 0, S_START = 1, S_NEWTON = 2;
 
 struct Bucket {
     int L = 0, nb = 0;
@@ -241,12 +253,15 @@ struct sphnse_ensemble {
     double2 *alpha = nullptr, *dif = nullptr, *y0 = nullptr, *psi = nullptr, *d = nullptr, *ynew = nullptr,
             *F = nullptr;
     InstPar* d_par = nullptr;
-    std::vector<InstPar> par;
+    InstPar* par = nullptr;          // pinned host copy, uploaded before each launch
+    int2* d_btab = nullptr;          // block table (instance, block of the instance)
+    int nbt = 0;
     unsigned long long* d_norms = nullptr;
     unsigned long long* h_norms = nullptr;
     std::vector<Ctl> ctl;
-    cudaGraphExec_t g_rhs_alpha = nullptr, g_newton = nullptr;
+    cudaGraphExec_t g_rhs_alpha = nullptr, g_round = nullptr;
     int max_n = 0;
+    long rounds = 0;                 // graph launches of the last advance
 };
 
 namespace {
@@ -284,10 +299,8 @@ int batched_rhs(sphnse_ensemble* E, const double2* x, double2* F) {
     return SPHNSE_OK;
 }
 
-dim3 egrid(const sphnse_ensemble* E) { return dim3((E->max_n + 255) / 256, E->n); }
-
 int upload_par(sphnse_ensemble* E) {
-    return cudaMemcpyAsync(E->d_par, E->par.data(), E->n * sizeof(InstPar), cudaMemcpyHostToDevice, E->stream) ==
+    return cudaMemcpyAsync(E->d_par, E->par, E->n * sizeof(InstPar), cudaMemcpyHostToDevice, E->stream) ==
                    cudaSuccess
                ? SPHNSE_OK
                : SPHNSE_E_CUDA;
@@ -327,7 +340,9 @@ void destroy_ens(sphnse_ensemble* E) {
     if (E->stream) cudaStreamSynchronize(E->stream);
     else cudaDeviceSynchronize();
     if (E->g_rhs_alpha) cudaGraphExecDestroy(E->g_rhs_alpha);
-    if (E->g_newton) cudaGraphExecDestroy(E->g_newton);
+    if (E->g_round) cudaGraphExecDestroy(E->g_round);
+    if (E->par) cudaFreeHost(E->par);
+    if (E->d_btab) cudaFree(E->d_btab);
     if (E->ev_in) cudaEventDestroy(E->ev_in);
     if (E->ev_out) cudaEventDestroy(E->ev_out);
     for (auto& B : E->buckets) {
@@ -483,6 +498,18 @@ sphnse_ensemble* sphnse_ensemble_create(int n, const int* Ls, const double* nus,
     if (!rc && cudaMallocHost(reinterpret_cast<void**>(&E->h_norms), size_t(n) * 8 * sizeof(unsigned long long)) !=
                    cudaSuccess)
         rc = SPHNSE_E_NOMEM;
+    if (!rc && cudaMallocHost(reinterpret_cast<void**>(&E->par), size_t(n) * sizeof(InstPar)) != cudaSuccess)
+        rc = SPHNSE_E_NOMEM;
+    if (!rc) {
+        std::vector<int2> bt;
+        for (int i = 0; i < n; ++i)
+            for (int b = 0; b < (E->nco[i] + EB - 1) / EB; ++b) bt.push_back(make_int2(i, b));
+        E->nbt = int(bt.size());
+        if (cudaMalloc(reinterpret_cast<void**>(&E->d_btab), bt.size() * sizeof(int2)) != cudaSuccess)
+            rc = SPHNSE_E_NOMEM;
+        else
+            cudaMemcpy(E->d_btab, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    }
     if (rc) {
         destroy_ens(E);
         return nullptr;
@@ -494,7 +521,6 @@ sphnse_ensemble* sphnse_ensemble_create(int n, const int* Ls, const double* nus,
         return nullptr;
     }
     for (auto& B : E->buckets) B.P->stream = E->stream;
-    E->par.resize(n);
     E->ctl.resize(n);
     for (int i = 0; i < n; ++i) {
         InstPar& p = E->par[i];
@@ -534,8 +560,8 @@ static int set_precision(sphnse_ensemble* E, int prec) {
         B.tc = want;
     }
     if (E->g_rhs_alpha) cudaGraphExecDestroy(E->g_rhs_alpha);
-    if (E->g_newton) cudaGraphExecDestroy(E->g_newton);
-    E->g_rhs_alpha = E->g_newton = nullptr;
+    if (E->g_round) cudaGraphExecDestroy(E->g_round);
+    E->g_rhs_alpha = E->g_round = nullptr;
     E->precision = prec;
     return SPHNSE_OK;
 }
@@ -551,6 +577,21 @@ int sphnse_ensemble_set(sphnse_ensemble* E, int key, double v) {
         case SPHNSE_KEY_PRECISION: return set_precision(E, int(v));
         default: return SPHNSE_E_ARG;
     }
+}
+
+int sphnse_ensemble_get(sphnse_ensemble* E, int key, double* v) {
+    if (!E || !v) return SPHNSE_E_ARG;
+    switch (key) {
+        case SPHNSE_KEY_RTOL: *v = E->rtol; break;
+        case SPHNSE_KEY_ATOL: *v = E->atol; break;
+        case SPHNSE_KEY_MAX_ORDER: *v = E->max_order; break;
+        case SPHNSE_KEY_NEWTON_MAX_ITER: *v = E->newton_max; break;
+        case SPHNSE_KEY_H_MAX: *v = E->h_max; break;
+        case SPHNSE_KEY_PRECISION: *v = E->precision; break;
+        case SPHNSE_KEY_ROUNDS: *v = double(E->rounds); break;
+        default: return SPHNSE_E_ARG;
+    }
+    return SPHNSE_OK;
 }
 
 int sphnse_ensemble_instance(sphnse_ensemble* E, int i, double** alpha, double** F, int* n_coeff) {
@@ -577,13 +618,13 @@ static int ensemble_init_inner(sphnse_ensemble* E, double t0) {
     int rc;
     if ((rc = ensemble_rhs_inner(E))) return rc;
     const double thr = E->atol / E->rtol;
-    for (auto& p : E->par) {
-        p.active = 1;
-        p.thr = thr;
+    for (int i = 0; i < E->n; ++i) {
+        E->par[i].flags = F_INIT;
+        E->par[i].thr = thr;
     }
     if ((rc = upload_par(E))) return rc;
     cudaMemsetAsync(E->d_norms, 0, size_t(E->n) * 8 * sizeof(unsigned long long), E->stream);
-    kb_wnorm<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->F, E->alpha, E->d_norms, 0);
+    kb_wnorm<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, F_INIT, E->F, E->alpha, E->d_norms, 0);
     if ((rc = read_all_norms(E))) return rc;
     for (int i = 0; i < E->n; ++i) {
         if (E->h_norms[size_t(i) * 8 + 7]) return SPHNSE_E_NONFINITE;
@@ -598,7 +639,7 @@ static int ensemble_init_inner(sphnse_ensemble* E, double t0) {
         E->par[i].h0 = h0;
     }
     if ((rc = upload_par(E))) return rc;
-    kb_init<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->dif, E->F);
+    kb_init<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, E->dif, E->F);
     return check_cuda(cudaGetLastError());
 }
 
@@ -608,15 +649,21 @@ int sphnse_ensemble_init(sphnse_ensemble* E, double t0) {
     return leave(E, ensemble_init_inner(E, t0));
 }
 
-static int ensemble_step_inner(sphnse_ensemble* E, sphnse_step_info* info);
+static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_info* info);
 
 int sphnse_ensemble_step(sphnse_ensemble* E, sphnse_step_info* info) {
     if (!E) return SPHNSE_E_ARG;
     enter(E);
-    return leave(E, ensemble_step_inner(E, info));
+    return leave(E, ensemble_advance_inner(E, 1, info));
 }
 
-static int ensemble_step_inner(sphnse_ensemble* E, sphnse_step_info* info) {
+int sphnse_ensemble_advance(sphnse_ensemble* E, int nsteps, sphnse_step_info* info) {
+    if (!E || nsteps < 0) return SPHNSE_E_ARG;
+    enter(E);
+    return leave(E, ensemble_advance_inner(E, nsteps, info));
+}
+
+static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_info* info) {
     const int n = E->n;
     double gam[SPHNSE_MAXK], iga[SPHNSE_MAXK], ec[SPHNSE_MAXK];
     {
@@ -630,126 +677,138 @@ static int ensemble_step_inner(sphnse_ensemble* E, sphnse_step_info* info) {
     }
     const double thr = E->atol / E->rtol;
     const int maxit = E->newton_max;
+    const size_t nb = size_t(n) * 8 * sizeof(unsigned long long);
     int rc;
-    for (auto& c : E->ctl) {
-        c.done = false;
+    // one round: accept / rescale / predict where flagged, the batched RHS at
+    // ynew, the Newton update where flagged, and the norms to the host
+    rc = capture(E, &E->g_round, [&]() {
+        cudaStream_t st = E->stream;
+        if (cudaMemsetAsync(E->d_norms, 0, nb, st) != cudaSuccess) return SPHNSE_E_CUDA;
+        kb_accept<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
+        kb_rescale<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif);
+        kb_predict<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew);
+        kb_wnorm<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, F_PREDICT, E->alpha, E->alpha, E->d_norms, 4);
+        int r = batched_rhs(E, E->ynew, E->F);
+        if (r) return r;
+        kb_newton<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->F, E->alpha, E->y0, E->psi, E->d, E->ynew,
+                                          E->dif, E->d_norms);
+        if (cudaMemcpyAsync(E->h_norms, E->d_norms, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return SPHNSE_E_CUDA;
+        return check_cuda(cudaGetLastError());
+    });
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        Ctl& c = E->ctl[i];
+        c.state = nsteps > 0 ? S_START : S_IDLE;
+        c.steps_left = nsteps;
+        c.attempts = 0;
         c.nofailed = true;
+        c.pending_accept = false;
         c.rejections = 0;
         c.newton = 0;
         c.h_dif_before = c.h_dif;
     }
-    // Newton iteration graph: batched RHS of all instances at ynew + masked update
-    rc = capture(E, &E->g_newton, [&]() {
-        int r = batched_rhs(E, E->ynew, E->F);
-        if (r) return r;
-        kb_newton<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->F, E->alpha, E->y0, E->psi, E->d, E->ynew, E->dif,
-                                                   E->d_norms);
-        return check_cuda(cudaGetLastError());
-    });
-    if (rc) return rc;
-    for (int attempt = 0; attempt < 200; ++attempt) {
-        int pending = 0;
+    E->rounds = 0;
+    for (;;) {
+        bool newton = false, accept = false;
         for (int i = 0; i < n; ++i) {
             Ctl& c = E->ctl[i];
             InstPar& p = E->par[i];
-            p.active = 0;
-            p.rescale = 0;
-            c.attempting = false;
-            if (c.done) continue;
-            ++pending;
-            c.hmin = 16.0 * EPS * std::fabs(c.t);
-            double h = std::min(E->h_max, std::max(c.hmin, c.h));
-            c.h = h;
-            const int k = c.k;
-            if (h != c.h_dif) {
-                rescale_mat(k, h / c.h_dif, p.A);
-                p.rescale = 1;
-                c.h_dif = h;
-                c.nconhk = 0;
+            p.flags = 0;
+            if (c.pending_accept) {
+                p.flags |= F_ACCEPT;
+                p.ka = c.acc_k;
+                c.pending_accept = false;
+                accept = true;
             }
-            if (h != c.miter_h || k != c.miter_k) {
-                c.havrate = 0;
-                c.miter_h = h;
-                c.miter_k = k;
+            if (c.state == S_START) {
+                if (++c.attempts > 200) return SPHNSE_E_STEP_TOO_SMALL;
+                c.hmin = 16.0 * EPS * std::fabs(c.t);
+                const double h = std::min(E->h_max, std::max(c.hmin, c.h));
+                c.h = h;
+                const int k = c.k;
+                if (h != c.h_dif) {
+                    rescale_mat(k, h / c.h_dif, p.A);
+                    p.flags |= F_RESCALE;
+                    c.h_dif = h;
+                    c.nconhk = 0;
+                }
+                if (h != c.miter_h || k != c.miter_k) {
+                    c.havrate = 0;
+                    c.miter_h = h;
+                    c.miter_k = k;
+                }
+                c.ha = h;
+                c.ka = k;
+                p.k = k;
+                p.c = h * iga[k - 1];
+                p.thr = thr;
+                for (int j = 0; j < SPHNSE_MAXK; ++j) p.g[j] = j < k ? gam[j] * iga[k - 1] : 0.0;
+                p.flags |= F_PREDICT | F_NEWTON;
+                c.state = S_NEWTON;
+                c.it = 0;
+                c.its = 0;
+                c.oldnrm = 0.0;
+                c.conv = false;
+            } else if (c.state == S_NEWTON) {
+                p.flags |= F_NEWTON;
             }
-            c.ha = h;
-            c.ka = k;
-            p.k = k;
-            p.c = h * iga[k - 1];
-            p.thr = thr;
-            for (int j = 0; j < SPHNSE_MAXK; ++j) p.g[j] = j < k ? gam[j] * iga[k - 1] : 0.0;
-            p.active = 1;
-            c.attempting = true;
-            c.in_newton = true;
-            c.conv = false;
-            c.its = 0;
-            c.oldnrm = 0.0;
+            newton = newton || (p.flags & F_NEWTON);
         }
-        if (!pending) break;
+        if (!newton) {
+            // only the accepts of the last round remain
+            if (accept) {
+                if ((rc = upload_par(E))) return rc;
+                kb_accept<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
+                if ((rc = check_cuda(cudaGetLastError()))) return rc;
+            }
+            break;
+        }
         if ((rc = upload_par(E))) return rc;
-        kb_rescale<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->dif);
-        kb_predict<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew);
-        cudaMemsetAsync(E->d_norms, 0, size_t(n) * 8 * sizeof(unsigned long long), E->stream);
-        kb_wnorm<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->alpha, E->alpha, E->d_norms, 4);
-        if ((rc = check_cuda(cudaGetLastError()))) return rc;
-        for (int it = 0; it < maxit; ++it) {
-            bool any = false;
-            for (int i = 0; i < n; ++i) {
-                E->par[i].active = E->ctl[i].attempting && E->ctl[i].in_newton;
-                any = any || E->par[i].active;
-            }
-            if (!any) break;
-            if ((rc = upload_par(E))) return rc;
-            // slot 4 (the weight norm of alpha) is only read at it == 0
-            if (it > 0) cudaMemsetAsync(E->d_norms, 0, size_t(n) * 8 * sizeof(unsigned long long), E->stream);
-            if (cudaGraphLaunch(E->g_newton, E->stream) != cudaSuccess) return SPHNSE_E_CUDA;
-            if ((rc = read_all_norms(E))) return rc;
-            for (int i = 0; i < n; ++i) {
-                Ctl& c = E->ctl[i];
-                if (!E->par[i].active) continue;
-                if (E->h_norms[size_t(i) * 8 + 7]) return SPHNSE_E_NONFINITE;
-                if (it == 0) c.ynorm = nrm(E, i, 4);
-                for (int q = 0; q < 4; ++q) c.nrm[q] = nrm(E, i, q);
-                c.its = it + 1;
-                const double newnrm = c.nrm[0], minnrm = 100.0 * EPS * c.ynorm;
-                bool stop = false, conv = false;
-                if (newnrm <= minnrm) {
-                    stop = conv = true;
-                } else if (it == 0) {
-                    if (c.havrate) {
-                        const double errit = newnrm * c.rate / (1.0 - c.rate);
-                        if (errit <= 0.05 * E->rtol) stop = conv = true;
-                    } else {
-                        c.rate = 0.0;
-                    }
-                } else if (newnrm > 0.9 * c.oldnrm) {
-                    stop = true;
-                } else {
-                    c.rate = std::max(0.9 * c.rate, newnrm / c.oldnrm);
-                    c.havrate = 1;
-                    const double errit = newnrm * c.rate / (1.0 - c.rate);
-                    if (errit <= 0.5 * E->rtol) stop = conv = true;
-                    else if (it == maxit - 1) stop = true;
-                    else if (0.5 * E->rtol < errit * std::pow(c.rate, maxit - 1 - it)) stop = true;
-                }
-                c.oldnrm = newnrm;
-                if (stop) {
-                    c.in_newton = false;
-                    c.conv = conv;
-                }
-            }
-        }
-        // decisions
-        bool any_accept = false;
+        if (cudaGraphLaunch(E->g_round, E->stream) != cudaSuccess || cudaStreamSynchronize(E->stream) != cudaSuccess)
+            return SPHNSE_E_CUDA;
+        ++E->rounds;
         for (int i = 0; i < n; ++i) {
             Ctl& c = E->ctl[i];
-            InstPar& p = E->par[i];
-            p.active = 0;
-            if (!c.attempting) continue;
+            if (!(E->par[i].flags & F_NEWTON)) continue;
+            if (E->h_norms[size_t(i) * 8 + 7]) return SPHNSE_E_NONFINITE;
+            const int it = c.it;
+            if (it == 0) c.ynorm = nrm(E, i, 4);
+            for (int q = 0; q < 4; ++q) c.nrm[q] = nrm(E, i, q);
+            c.its = it + 1;
+            // the corrector's rate test (as sphnse_step)
+            const double newnrm = c.nrm[0], minnrm = 100.0 * EPS * c.ynorm;
+            bool stop = false, conv = false;
+            if (newnrm <= minnrm) {
+                stop = conv = true;
+            } else if (it == 0) {
+                if (c.havrate) {
+                    const double errit = newnrm * c.rate / (1.0 - c.rate);
+                    if (errit <= 0.05 * E->rtol) stop = conv = true;
+                } else {
+                    c.rate = 0.0;
+                }
+            } else if (newnrm > 0.9 * c.oldnrm) {
+                stop = true;
+            } else {
+                c.rate = std::max(0.9 * c.rate, newnrm / c.oldnrm);
+                c.havrate = 1;
+                const double errit = newnrm * c.rate / (1.0 - c.rate);
+                if (errit <= 0.5 * E->rtol) stop = conv = true;
+                else if (it == maxit - 1) stop = true;
+                else if (0.5 * E->rtol < errit * std::pow(c.rate, maxit - 1 - it)) stop = true;
+            }
+            c.oldnrm = newnrm;
+            if (!stop && it + 1 < maxit) {
+                c.it = it + 1;
+                continue;
+            }
+            // the attempt is over
             c.newton += c.its;
             const double h = c.ha;
             const int k = c.ka;
-            if (!c.conv) {
+            c.state = S_START;
+            if (!conv) {
                 ++c.rejections;
                 if (h <= c.hmin) return SPHNSE_E_STEP_TOO_SMALL;
                 c.h = std::max(c.hmin, 0.3 * h);
@@ -776,11 +835,9 @@ static int ensemble_step_inner(sphnse_ensemble* E, sphnse_step_info* info) {
                 }
                 continue;
             }
-            // accepted
-            p.active = 1;
-            p.k = k;
-            any_accept = true;
-            c.done = true;
+            // accepted: the differences are updated at the start of the next launch
+            c.pending_accept = true;
+            c.acc_k = k;
             c.t += h;
             c.nconhk = std::min(c.nconhk + 1, SPHNSE_MAXK + 2);
             if (c.nconhk >= k + 2) {
@@ -826,15 +883,12 @@ static int ensemble_step_inner(sphnse_ensemble* E, sphnse_step_info* info) {
                 o.next_h = c.h;
                 o.h_dif_before = c.h_dif_before;
             }
-        }
-        if (any_accept) {
-            if ((rc = upload_par(E))) return rc;
-            kb_accept<<<egrid(E), 256, 0, E->stream>>>(E->d_par, E->dif, E->d, E->alpha, E->ynew);
-            if ((rc = check_cuda(cudaGetLastError()))) return rc;
+            c.nofailed = true;
+            c.attempts = 0;
+            c.h_dif_before = c.h_dif;
+            if (--c.steps_left == 0) c.state = S_IDLE;
         }
     }
-    for (const auto& c : E->ctl)
-        if (!c.done) return SPHNSE_E_STEP_TOO_SMALL;
     return SPHNSE_OK;
 }
 

@@ -507,7 +507,6 @@ struct TcSynArgs {
     int N, nh, nlat, nblk, pairs;
     int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
     size_t sgs;
-    int m0phi;                   // u_phi at m = 0 from columns 12..15 of the order-1 item (k_prep_tc)
 };
 
 constexpr int TC_SYN_MAXNS = 8;
@@ -527,9 +526,10 @@ __host__ __device__ inline int syn_tailw(int N, int m, int par) {
 
 // Item = (order m, latitude tile of 128 northern nodes, group of ng
 // instances): both parities into their own accumulator of brows columns
-// (12 per instance: six hi parts, six lo parts of the coefficient sets; hi
-// and lo table parts go into the same accumulator, as both multiply the same
-// B tile), so one A tile serves every instance of the group.  K chunks of 16
+// (12 per instance: six hi parts, six lo parts of the coefficient sets; then
+// two per instance for u_phi at m = 0, filled on order-1 tiles only; hi and
+// lo table parts go into the same accumulator, as both multiply the same B
+// tile), so one A tile serves every instance of the group.  K chunks of 16
 // degrees past the block are skipped.
 // NS stages (a compile-time ring keeps the per-stage index arithmetic of the
 // single-thread producer and MMA issuer cheap); SINGLE: one instance, 16 B rows
@@ -665,22 +665,21 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 tmem_ld4_nowait(ce + 8, e + 8);
                 tmem_ld8_nowait(co, o);
                 tmem_ld4_nowait(co + 8, o + 8);
-                const bool phi0 = a.m0phi && m == 1;   // uniform over the item
-                uint32_t pe[4], po[4];
-                if (phi0) {
-                    tmem_ld4_nowait(ce + 12, pe);
-                    tmem_ld4_nowait(co + 12, po);
+                // u_phi at m = 0: columns 12 ng + 2 q (hi, lo) of the order-1 item
+                uint32_t pe[2], po[2];
+                if (m == 1) {   // uniform over the item
+                    const uint32_t cp = uint32_t(12 * (SINGLE ? 1 : a.ng) + 2 * q);
+                    tmem_ld2_nowait(tmem + lanes + uint32_t((buf * 2 + 0) * brows) + cp, pe);
+                    tmem_ld2_nowait(tmem + lanes + uint32_t((buf * 2 + 1) * brows) + cp, po);
                 }
                 tmem_wait_ld();
                 if (!ok || p >= nh || *abort) continue;
-                if (phi0) {
-                    const float er = __uint_as_float(pe[0]) + __uint_as_float(pe[2]);
-                    const float ei = __uint_as_float(pe[1]) + __uint_as_float(pe[3]);
-                    const float orr = __uint_as_float(po[0]) + __uint_as_float(po[2]);
-                    const float oi = __uint_as_float(po[1]) + __uint_as_float(po[3]);
+                if (m == 1) {
+                    const float ev = __uint_as_float(pe[0]) + __uint_as_float(pe[1]);
+                    const float ov = __uint_as_float(po[0]) + __uint_as_float(po[1]);
                     float2* o0 = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
-                    o0[gsyn_index(a.pairs, 2, 0, p, N, nlat)] = make_float2(er + orr, ei + oi);
-                    if (nlat - 1 - p != p) o0[gsyn_index(a.pairs, 2, 0, nlat - 1 - p, N, nlat)] = make_float2(er - orr, ei - oi);
+                    o0[gsyn_index(a.pairs, 2, 0, p, N, nlat)] = make_float2(ev + ov, 0.f);
+                    if (nlat - 1 - p != p) o0[gsyn_index(a.pairs, 2, 0, nlat - 1 - p, N, nlat)] = make_float2(ev - ov, 0.f);
                 }
                 float E[6], O[6];
 #pragma unroll
@@ -696,7 +695,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                     const float sg = hemi == 0 ? 1.f : -1.f;
 #pragma unroll
                     for (int f = 0; f < 3; ++f) {
-                        if (f == 2 && m == 0 && a.m0phi) break;   // written by the order-1 item
+                        if (f == 2 && m == 0) break;   // written by the order-1 item
                         const float gr = E[2 * f] + sg * O[2 * f];
                         const float gi = E[2 * f + 1] + sg * O[2 * f + 1];
                         float2 ov;
@@ -728,8 +727,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
 // r0 = 12 (instance mod ng), of its group's tile (rows past the group's
 // instances stay zero).  All of a thread's loads are independent.
 //
-// m0phi (one instance per 16-row tile): the order-1 tiles also carry, in rows
-// 12..15 (hi re, hi im, lo re, lo im), the column -a_{K,0}.  With
+// Every instance also has two rows 12 ng + 2 (instance mod ng) (hi, lo) that
+// only the order-1 tiles fill, with the real column -a_{K,0}.  With
 // d/dtheta Pt_K^0 = sqrt(K (K+1)) Pt_K^1 (ladder relation, Condon-Shortley
 // phase), u_phi at m = 0 is -sum_K alpha_{K,0} Pt_K^1: a sum over the
 // order-1 table that needs no division by sin(theta).  The degree-shift form
@@ -737,7 +736,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
 // split's rounding would be amplified by 1 / sin(theta).
 __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
                                                  unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
-                                                 int ntiles, int N, int n_coeff, int ng, int brows, int m0phi) {
+                                                 int ntiles, int N, int n_coeff, int ng, int brows) {
     pdl_launch();
     pdl_wait();   // alpha may be the predecessor's output
     const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
@@ -781,21 +780,17 @@ __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alp
         *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + c, q)) = pack_hi(v[c]);
         *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + 6 + c, q)) = pack_lo(v[c]);
     }
-    if (m0phi && m == 1) {
-        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N
-        float re[8], im[8];
+    if (m == 1) {
+        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N (real)
+        float re[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int K = K0 + 2 * e;
-            double2 u = make_double2(0.0, 0.0);
-            if (j0 + e < n && K <= N) u = a0[K];
-            re[e] = -float(u.x);
-            im[e] = -float(u.y);
+            re[e] = (j0 + e < n && K <= N) ? -float(a0[K].x) : 0.f;
         }
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(12, q)) = pack_hi(re);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(13, q)) = pack_hi(im);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(14, q)) = pack_lo(re);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(15, q)) = pack_lo(im);
+        const int rp = 12 * ng + 2 * (inst % ng);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp, q)) = pack_hi(re);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp + 1, q)) = pack_lo(re);
     }
 }
 
@@ -1029,8 +1024,8 @@ int tc_setup_synthesis(sphnse_plan* P) {
     return check_cuda(cudaGetLastError());
 }
 
-// Instance groups of a batch of nb instances of one truncation: ng <= 10
-// instances share every A tile (MMA N = brows = 12 ng rounded up to 16),
+// Instance groups of a batch of nb instances of one truncation: ng <= 9
+// instances share every A tile (MMA N = brows = 14 ng rounded up to 16),
 // B tiles [group][tile][brows][64], items (m, latitude tile, group) in LPT
 // order over one CTA per SM.
 int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
@@ -1038,10 +1033,12 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
     const int N = P->N, nh = P->nh;
     TcBatch T;
     T.nb = nb;
-    T.ng = std::min(nb, 10);
+    // 14 B rows per instance (12 coefficient rows, 2 for u_phi at m = 0); two
+    // accumulators of brows <= 128 columns per buffer fit TMEM's 512
+    T.ng = std::min(nb, 9);
     T.ngroups = (nb + T.ng - 1) / T.ng;
     T.ng = (nb + T.ngroups - 1) / T.ngroups;   // balanced groups
-    T.brows = ((12 * T.ng + 15) / 16) * 16;
+    T.brows = ((14 * T.ng + 15) / 16) * 16;
     const size_t stage = 2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2;
     T.ns = int(std::min<size_t>(6, (size_t(227) * 1024 - 1024 - 512) / stage));
     const size_t bytes = size_t(T.ngroups) * P->tc.ntiles * T.brows * TC_TILE_K * 2;
@@ -1094,15 +1091,12 @@ void tc_batch_free(TcBatch* B) {
     *B = TcBatch();
 }
 
-// the m = 0 u_phi column fits when every group is one instance in 16 B rows
-static int tc_m0phi(const TcBatch& B) { return B.ng == 1 && B.brows == 16 ? 1 : 0; }
-
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) {
     stage_begin(P, SPHNSE_STAGE_PREP);
     const cudaError_t e = launch_pdl(k_prep_tc, dim3((P->tc.ntiles + 15) / 16, B.nb), dim3(128), 0, P->stream,
                                      reinterpret_cast<const double2*>(alpha), static_cast<const float4*>(P->d_prepc32),
                                      B.btiles, static_cast<const int2*>(P->tc.tile_info), P->tc.ntiles, P->N,
-                                     P->n_coeff, B.ng, B.brows, tc_m0phi(B));
+                                     P->n_coeff, B.ng, B.brows);
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(e);
 }
@@ -1118,7 +1112,7 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
                 P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
-                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2, tc_m0phi(B)};
+                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     const cudaError_t e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);

@@ -22,6 +22,8 @@
 #include <vector>
 
 #include "internal.h"
+#include "dmath.cuh"
+#include "newton.cuh"
 #include "reduce.cuh"
 
 namespace sph {
@@ -81,7 +83,6 @@ inline double d2u_max(unsigned long long v) {
 // ---------------------------------------------------------------------------
 // device kernels (one thread per packed complex entry)
 
-__device__ __forceinline__ double wmax(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
 __global__ void k_zero_dif(double2* dif, const double2* F, double h, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +98,7 @@ __global__ void k_wnorm(const double2* v, const double2* y, double thr, unsigned
     double r[1] = {0.0};
     if (i < n) {
         const double2 a = v[i], b = y[i];
-        r[0] = fmax(fabs(a.x) / fmax(fabs(b.x), thr), fabs(a.y) / fmax(fabs(b.y), thr));
+        r[0] = fmax(fabs(a.x) * rcp64<1>(fmax(fabs(b.x), thr)), fabs(a.y) * rcp64<1>(fmax(fabs(b.y), thr)));
     }
     const int id[1] = {idx};
     block_amax<1>(slots, r, id);
@@ -146,33 +147,19 @@ __global__ void k_newton(const double2* F, const double2* y, const double2* y0, 
                          double2* ynew, const double2* dkm1, const double2* dk, const int2* lm, double c,
                          double nu, double Omega, double thr, unsigned long long* slot, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double nv[4] = {0.0, 0.0, 0.0, 0.0};
+    float nv[4] = {0.f, 0.f, 0.f, 0.f};
+    bool bad = false;
     if (i < n) {
-        const int L = lm[i].x, m = lm[i].y;
-        const double lam = double(L) * (L + 1.0);
-        // 1 - c J_d = (1 + c nu lam) - i c 2 Omega m / lam
-        const double mr = 1.0 + c * nu * lam, mi = -c * 2.0 * Omega * m / lam;
-        const double2 f = F[i], ps = psi[i], dd = d[i], yo = y[i], yn = ynew[i], a0 = y0[i];
-        const double rx = c * f.x - (ps.x + dd.x), ry = c * f.y - (ps.y + dd.y);
-        const double den = mr * mr + mi * mi;
-        const double dlx = (rx * mr + ry * mi) / den, dly = (ry * mr - rx * mi) / den;
-        const double wx = wmax(fabs(yo.x), fabs(yn.x), thr), wy = wmax(fabs(yo.y), fabs(yn.y), thr);
-        nv[0] = fmax(fabs(dlx) / wx, fabs(dly) / wy);
-        const double2 dn = make_double2(dd.x + dlx, dd.y + dly);
-        const double2 yv = make_double2(a0.x + dn.x, a0.y + dn.y);
-        d[i] = dn;
-        ynew[i] = yv;
-        const double vx = wmax(fabs(yo.x), fabs(yv.x), thr), vy = wmax(fabs(yo.y), fabs(yv.y), thr);
-        nv[1] = fmax(fabs(dn.x) / vx, fabs(dn.y) / vy);
-        if (dkm1) {
-            const double2 q = dkm1[i];
-            nv[2] = fmax(fabs(q.x + dn.x) / vx, fabs(q.y + dn.y) / vy);
-        }
-        const double2 r2 = dk[i];
-        nv[3] = fmax(fabs(dn.x - r2.x) / vx, fabs(dn.y - r2.y) / vy);
+        const int2 q = lm[i];
+        const NewtonEntry e = newton_entry(q.x, q.y, c, float(nu), float(2.0 * Omega), fmaxf(float(thr), 1e-30f),
+                                           F[i], psi[i], d[i], y[i], ynew[i], y0[i], dkm1 ? dkm1 + i : nullptr, dk[i]);
+        d[i] = e.dn;
+        ynew[i] = e.yv;
+        for (int j = 0; j < 4; ++j) nv[j] = e.nv[j];
+        bad = e.bad;
     }
     const int id[4] = {0, 1, 2, 3};
-    block_amax<4>(slot, nv, id);
+    block_amax_f<4>(slot, nv, id, bad);
 }
 
 // D_{k+1} = d - D_k; D_k = d; D_j += D_{j+1} (j = k-1..0); y = ynew
@@ -223,7 +210,7 @@ __global__ void k_adj_fixpoint(double2* mu, const double2* b, const double2* JT,
     if (i < n) {
         const int L = lm[i].x, m = lm[i].y;
         const double lam = double(L) * (L + 1.0);
-        const double mr = 1.0 + c * nu * lam, mi = c * 2.0 * Omega * m / lam;  // conj(1 - c J_d)
+        const double mr = 1.0 + c * nu * lam, mi = c * 2.0 * Omega * m * rcp64<2>(lam);  // conj(1 - c J_d)
         const double2 bb = b[i];
         double rx, ry;
         double2 u = make_double2(0.0, 0.0);
@@ -237,9 +224,9 @@ __global__ void k_adj_fixpoint(double2* mu, const double2* b, const double2* JT,
             ry = bb.y - u.y + c * jt.y;
         }
         r[0] = fmax(fabs(rx), fabs(ry));
-        const double den = mr * mr + mi * mi;
-        u.x += (rx * mr + ry * mi) / den;
-        u.y += (ry * mr - rx * mi) / den;
+        const double iden = rcp64<2>(mr * mr + mi * mi);
+        u.x += (rx * mr + ry * mi) * iden;
+        u.y += (ry * mr - rx * mi) * iden;
         mu[i] = u;
     }
     const int id[1] = {0};

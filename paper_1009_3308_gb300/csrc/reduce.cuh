@@ -45,4 +45,37 @@ __device__ __forceinline__ void block_amax(unsigned long long* slots, const doub
     }
 }
 
+// FP32 form: the block maximum of NV non-negative floats into the slots
+// (converted to double once per block); bad (any thread) sets slots[7].
+template <int NV>
+__device__ __forceinline__ void block_amax_f(unsigned long long* slots, const float (&v)[NV], const int (&idx)[NV],
+                                             bool bad) {
+    __shared__ float redf[NV][32];
+    float x[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        x[j] = v[j];
+        if (!(x[j] <= 3.0e38f)) {
+            bad = true;
+            x[j] = 0.f;
+        }
+    }
+    if (bad) atomicMax(slots + 7, 1ull);
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[j] = fmaxf(x[j], __shfl_xor_sync(0xffffffffu, x[j], o));
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) redf[j][warp] = x[j];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int j = threadIdx.x;
+        float mx = redf[j][0];
+        for (int w = 1; w < nw; ++w) mx = fmaxf(mx, redf[j][w]);
+        if (mx > 0.f) atomicMax(slots + idx[j], static_cast<unsigned long long>(__double_as_longlong(double(mx))));
+    }
+}
+
 }  // namespace sph

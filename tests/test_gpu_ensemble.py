@@ -66,3 +66,36 @@ def test_ensemble_steps_equal_independent_integrators():
         ref = it.alpha.cpu().numpy()
         got = ens.get(i).cpu().numpy()
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), i
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_ensemble_advance_equals_independent_integrators(precision):
+    """sphnse_ensemble_advance: every instance takes its 15 steps at its own
+    pace in asynchronous rounds and ends where an integrator of its own ends
+    (same per-step decisions, so the same final time, order and state)."""
+    from paper_1009_3308_gb300 import Ensemble, Integrator, Plan
+    ens = Ensemble(LS, NUS, 1.0, precision=precision)
+    alphas = [coefficients(L, 1000 + i, 0.05) * 3 for i, L in enumerate(LS)]
+    for i, a in enumerate(alphas):
+        ens.set_alpha(i, _dev(a))
+    rt, at = 1e-6, 1e-10
+    ens.set("RTOL", rt)
+    ens.set("ATOL", at)
+    ens.init(0.0)
+    nsteps = 15
+    infos = ens.advance(nsteps)
+    for i, (L, nu) in enumerate(zip(LS, NUS)):
+        M = 3 * (L + 1)
+        p = Plan(L, M // 2, M, nu, 1.0, precision=precision)
+        p.set("RTOL", rt)
+        p.set("ATOL", at)
+        it = Integrator(p, _dev(alphas[i]))
+        refs = [it.step() for _ in range(nsteps)]
+        last = refs[-1]
+        assert infos[i]["order"] == last["order"], i
+        assert abs(infos[i]["t"] - last["t"]) <= 1e-12 * last["t"], i
+        assert infos[i]["rhs_evals"] == sum(r["rhs_evals"] for r in refs), i
+        assert infos[i]["rejections"] == sum(r["rejections"] for r in refs), i
+        ref = it.alpha.cpu().numpy()
+        got = ens.get(i).cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), i
