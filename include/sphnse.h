@@ -70,6 +70,8 @@ extern "C" {
                                          grid product; 0: in the product (default).
                                          Same F up to rounding; forward RHS only (the
                                          adjoint always carries it in the product) */
+#define SPHNSE_KEY_TIMING_PERIOD  11  /* stage timing records every period-th launch of a
+                                         timed stage (default 1) */
 #define SPHNSE_KEY_N_COEFF       100  /* read-only: n_coeff */
 #define SPHNSE_KEY_L             101  /* read-only: truncation degree */
 #define SPHNSE_KEY_NLAT          102  /* read-only */
@@ -299,8 +301,10 @@ int sphnse_ensemble_advance(sphnse_ensemble* ens, int nsteps, sphnse_step_info* 
 /* enable = bit mask of stages (bit s = stage s; SPHNSE_STAGE_ALL for every
  * stage): record a CUDA event pair on the plan's stream around every later
  * kernel launch of an enabled stage; enable == 0: stop and keep totals.
- * Enabling clears the totals.  Every event pair costs stream time, so a
- * throughput measurement should enable only the stage it reports. */
+ * Enabling clears the totals.  Every event pair costs stream time (the kernel
+ * after it cannot start before the pair's kernel completes), so a throughput
+ * measurement should enable only the stage it reports, and may time only
+ * every period-th launch of it (SPHNSE_KEY_TIMING_PERIOD). */
 int sphnse_stage_timing(sphnse_plan* plan, int enable);
 
 /* Synchronise the plan's stream, fold the recorded events into totals and

@@ -186,6 +186,9 @@ struct sphnse_plan {
 
     // optional per-stage CUDA-event timing on the plan's stream
     unsigned timing = 0;         // bit mask of timed stages
+    int timing_period = 1;       // record every timing_period-th launch of a timed stage
+    long stage_calls[8] = {};    // launches seen per stage while timed
+    bool stage_rec[8] = {};      // the current launch of the stage is recorded
     std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];
     int ev_used[SPHNSE_NSTAGES] = {0};
     double stage_ms[SPHNSE_NSTAGES] = {0};
@@ -250,11 +253,19 @@ void stage_begin(sphnse_plan* P, int stage);
 void stage_end(sphnse_plan* P, int stage);
 int check_cuda(cudaError_t e);
 
+// Ask once per kernel for the largest shared-memory carveout.  An SM runs
+// CTAs of different kernels together only under one L1/shared split: when a
+// small kernel (no shared memory) prefers the default split, the next
+// kernel's CTAs that need ~200 KB cannot start on an SM until it drains,
+// which defeats the early launch below.
+void prefer_max_smem(const void* kernel);
+
 // Launch with programmatic stream serialisation (the kernel calls pdl_wait()
 // before it reads what its predecessor on the stream wrote).
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
                               Args... args) {
+    prefer_max_smem(reinterpret_cast<const void*>(kernel));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;

@@ -580,9 +580,13 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
 
     if (warp == 0) {
         if (lane == 0) {
-            pdl_wait();
+            // the table tiles of the first ns stages do not depend on the
+            // predecessor (the B tiles do): they are requested before the wait,
+            // overlapping the coefficient prep, and their B tiles right after it
             const uint64_t pol = policy_evict_first();
             const uint64_t polb = policy_evict_last();
+            const unsigned char* pend[NS];
+            bool waited = false;
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
@@ -594,7 +598,16 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                         a.btiles + (size_t(g) * a.ntiles + size_t(a.tile_off[b])) * size_t(bbytes);
                     for (int kt = 0; kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
-                        if (it >= ns && !mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
+                        if (it >= ns) {
+                            if (!waited) {
+                                pdl_wait();
+                                // (an abort may have left a stage without its pend entry)
+                                for (int j = 0; j < ns; ++j)
+                                    if (!*abort) bulk_g2s(Bs + j * bbytes, pend[j], uint32_t(bbytes), &a_full[j], polb);
+                                waited = true;
+                            }
+                            if (!mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
+                        }
                         if (*abort) continue;
                         const bool last = kt == nkt - 1;
                         const int w = last ? tw : TC_TILE_K;
@@ -602,9 +615,15 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                         mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2 + bbytes));
                         tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
                         tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                        bulk_g2s(Bs + s * bbytes, bsrc + size_t(kt) * bbytes, uint32_t(bbytes), &a_full[s], polb);
+                        if (waited) bulk_g2s(Bs + s * bbytes, bsrc + size_t(kt) * bbytes, uint32_t(bbytes), &a_full[s], polb);
+                        else pend[s] = bsrc + size_t(kt) * bbytes;
                     }
                 }
+            }
+            if (!waited) {
+                pdl_wait();
+                for (int j = 0; j < it && j < ns; ++j)
+                    if (!*abort) bulk_g2s(Bs + j * bbytes, pend[j], uint32_t(bbytes), &a_full[j], polb);
             }
             for (int k = it - ns; k < it; ++k)
                 if (k >= 0) mbar_wait(&a_full[k % ns], (k / ns) & 1, abort, a.status);

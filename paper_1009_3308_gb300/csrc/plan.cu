@@ -3,6 +3,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <unordered_set>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,10 +46,14 @@ static void record_stage_event(sphnse_plan* P, int stage) {
 }
 
 void stage_begin(sphnse_plan* P, int stage) {
-    if (P->timing & (1u << stage)) record_stage_event(P, stage);
+    P->stage_rec[stage] = (P->timing & (1u << stage)) && P->stage_calls[stage] % P->timing_period == 0;
+    if (P->stage_rec[stage]) record_stage_event(P, stage);
 }
 void stage_end(sphnse_plan* P, int stage) {
-    if (P->timing & (1u << stage)) record_stage_event(P, stage);
+    if (!(P->timing & (1u << stage))) return;
+    if (P->stage_rec[stage]) record_stage_event(P, stage);
+    P->stage_rec[stage] = false;
+    ++P->stage_calls[stage];
 }
 
 static void free_tables(Tables& t) {
@@ -114,6 +121,14 @@ int ensure_tables(sphnse_plan* P, int prec) {
     }
     t.built = true;
     return SPHNSE_OK;
+}
+
+void prefer_max_smem(const void* kernel) {
+    static std::mutex mu;
+    static std::unordered_set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.insert(kernel).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 
 int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, double* out) {
@@ -395,6 +410,7 @@ int sphnse_plan_set(sphnse_plan* P, int key, double v) {
         case SPHNSE_KEY_H_MAX: if (v <= 0) return SPHNSE_E_ARG; P->h_max = v; return SPHNSE_OK;
         case SPHNSE_KEY_BDF: P->bdf = v != 0.0; return SPHNSE_OK;
         case SPHNSE_KEY_CORIOLIS_SPLIT: P->coriolis_split = v != 0.0; return SPHNSE_OK;
+        case SPHNSE_KEY_TIMING_PERIOD: if (v < 1 || v > 1e6) return SPHNSE_E_ARG; P->timing_period = int(v); return SPHNSE_OK;
         default: return SPHNSE_E_ARG;
     }
 }
@@ -412,6 +428,7 @@ int sphnse_plan_get(const sphnse_plan* P, int key, double* v) {
         case SPHNSE_KEY_H_MAX: *v = P->h_max; break;
         case SPHNSE_KEY_BDF: *v = P->bdf; break;
         case SPHNSE_KEY_CORIOLIS_SPLIT: *v = P->coriolis_split; break;
+        case SPHNSE_KEY_TIMING_PERIOD: *v = P->timing_period; break;
         case SPHNSE_KEY_N_COEFF: *v = P->n_coeff; break;
         case SPHNSE_KEY_L: *v = P->N; break;
         case SPHNSE_KEY_NLAT: *v = P->nlat; break;
@@ -484,6 +501,7 @@ int sphnse_stage_timing(sphnse_plan* P, int enable) {
         for (int s = 0; s < SPHNSE_NSTAGES; ++s) {
             P->stage_ms[s] = 0;
             P->stage_n[s] = 0;
+            P->stage_calls[s] = 0;
         }
     }
     P->timing = unsigned(enable) & ((1u << SPHNSE_NSTAGES) - 1);
