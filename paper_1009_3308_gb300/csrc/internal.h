@@ -128,6 +128,13 @@ struct TcState {
     TcBatch single;              // the plan's own instance
     size_t tsyn_bytes = 0;
     bool syn_ready = false;
+    // negligible table tiles: first significant synthesis K tile per (block,
+    // latitude tile) (the block's tile count if none), and max |Pt| per
+    // (table row, 64-latitude chunk)
+    int* syn_kt0 = nullptr;
+    int syn_nmt = 0;
+    std::vector<int> syn_kt0_host;
+    std::vector<float> chunk_max;
 };
 
 }  // namespace sph

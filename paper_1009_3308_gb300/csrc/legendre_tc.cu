@@ -85,6 +85,15 @@ struct TcAnaArgs {
 };
 
 constexpr int TC_ANA_NS = 5;                   // A stages
+
+// Table tiles whose entries are all below TC_SKIP in magnitude are not read:
+// near the poles Pt_K^m decays like sin(theta)^m below its turning point
+// sin(theta) = m / (K + 1/2), so at high order whole tiles of the polar
+// latitudes are negligible (about a tenth of the table at L = 511).  A
+// skipped term changes an output by at most TC_SKIP times the sum of the
+// skipped coefficients' magnitudes, six orders below the BF16 split's own
+// rounding (~1e-5).
+constexpr double TC_SKIP = 1e-11;
 constexpr int TC_ANA_BROWS = 32;               // B rows (N) per item at most
 constexpr int TC_ANA_BTILE = TC_ANA_BROWS * TC_TILE_K * 2;   // 4 KB per K tile
 constexpr int TC_ANA_COLS = 128;               // TMEM: 2 buffers x 64 columns
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
-                for (int kt = 0; kt < nkt; ++kt, ++it) {
+                for (int kt = itm.w >> 16; kt < nkt; ++kt, ++it) {
                     const int s = it % TC_ANA_NS;
                     if (it >= TC_ANA_NS && !mbar_wait(&a_empty[s], ((it / TC_ANA_NS) - 1) & 1, abort, a.status))
                         continue;
@@ -165,13 +174,14 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
-                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w);
+                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w & 0xFFFF);
+                const int kt0 = itm.w >> 16;
                 const int buf = i & 1, use = i >> 1;
                 bool ok = mbar_wait(&b_full[buf], use & 1, abort, a.status);
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status) && ok;
                 tc_fence_after();
                 const uint32_t d = tmem + uint32_t(buf * 64);
-                for (int kt = 0; kt < nkt; ++kt, ++it) {
+                for (int kt = kt0; kt < nkt; ++kt, ++it) {
                     const int s = it % TC_ANA_NS;
                     const bool okA = mbar_wait(&a_full[s], (it / TC_ANA_NS) & 1, abort, a.status);
                     tc_fence_after();
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
 #pragma unroll
                         for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
                             const uint64_t bd = sdesc_sw128(bt + kk * 32);
-                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt > kt0) || kk != 0);
                             mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                         }
                     }
@@ -200,12 +210,13 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             const int buf = i & 1;
             if (i >= 2) mbar_wait(&b_empty[buf], ((i >> 1) - 1) & 1, abort, a.status);
             const int4 itm = a.items[ib + i];
-            const int per_piece = nkt * 8 * NF;
+            const int kt0 = itm.w >> 16;
+            const int per_piece = (nkt - kt0) * 8 * NF;
             for (int task = ht; task < itm.z * per_piece; task += 128) {
                 const int j = task / per_piece, tl = task % per_piece;
                 const int4 pc = a.pieces[itm.y + j];
                 const int m = pc.x, par = pc.y;
-                const int f = tl % NF, q = (tl / NF) & 7, kt = tl / (8 * NF);
+                const int f = tl % NF, q = (tl / NF) & 7, kt = kt0 + tl / (8 * NF);
                 const int p0 = kt * TC_TILE_K + q * 8;
                 const float* g = a.gana + (size_t(f) * ld + m) * size_t(nlat) * 2;
                 float nv[16], sv[16];
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
             const int4 itm = a.items[ib + i];
             int4 sl = make_int4(0, 0, 0, 0);
             if (lane < itm.z) sl = a.slots[itm.y + lane];
-            for (int kt = 0; kt < nkt; ++kt, ++it) {
+            for (int kt = itm.w >> 16; kt < nkt; ++kt, ++it) {
                 const int s = it % TC_ANAB_NS;
                 int go = 0;
                 if (lane == 0) {
@@ -426,13 +437,14 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
-                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w);
+                const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w & 0xFFFF);
+                const int kt0 = itm.w >> 16;
                 const int buf = i & 1, use = i >> 1;
                 bool ok = true;
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 const uint32_t d = tmem + uint32_t(buf * 256);
-                for (int kt = 0; kt < nkt; ++kt, ++it) {
+                for (int kt = kt0; kt < nkt; ++kt, ++it) {
                     const int s = it % TC_ANAB_NS;
                     const bool okA = mbar_wait(&a_full[s], (it / TC_ANAB_NS) & 1, abort, a.status);
                     tc_fence_after();
@@ -440,7 +452,7 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
 #pragma unroll
                         for (int kk = 0; kk < TC_TILE_K / 16; ++kk) {
                             const uint64_t bd = sdesc_sw128(Bs + s * TC_ANAB_BBYTES + kk * 32);
-                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                            mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt > kt0) || kk != 0);
                             mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                         }
                     }
@@ -507,6 +519,8 @@ struct TcSynArgs {
     int N, nh, nlat, nblk, pairs;
     int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
     size_t sgs;
+    const int* kt0;              // first K tile per (block, latitude tile): [2 (N+1)][nmt]
+    int nmt;
 };
 
 constexpr int TC_SYN_MAXNS = 8;
@@ -596,7 +610,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                     const int tw = syn_tailw(N, m, par);
                     const unsigned char* bsrc =
                         a.btiles + (size_t(g) * a.ntiles + size_t(a.tile_off[b])) * size_t(bbytes);
-                    for (int kt = 0; kt < nkt; ++kt, ++it) {
+                    for (int kt = a.kt0[b * a.nmt + mt]; kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
                         if (it >= ns) {
                             if (!waited) {
@@ -633,15 +647,16 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const uint32_t idesc = idesc_bf16(TC_TILE_M, brows);
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int m = a.items[ib + i].x;
+                const int m = a.items[ib + i].x, mt = a.items[ib + i].y;
                 const int buf = i & 1, use = i >> 1;
                 bool ok = true;
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
                     const int nkt = syn_nkt(N, m, par), nd = syn_ndeg(N, m, par);
+                    const int kt0 = a.kt0[(2 * m + par) * a.nmt + mt];
                     const uint32_t d = tmem + uint32_t((buf * 2 + par) * brows);
-                    for (int kt = 0; kt < nkt; ++kt, ++it) {
+                    for (int kt = kt0; kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
                         const bool okA = mbar_wait(&a_full[s], (it / ns) & 1, abort, a.status);
                         tc_fence_after();
@@ -650,7 +665,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                         if (ok && okA && !*abort) {
                             for (int kk = 0; kk < nkk; ++kk) {
                                 const uint64_t bd = sdesc_sw128(Bs + s * bbytes + kk * 32);
-                                mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt | kk) != 0);
+                                mma_bf16(d, sdesc_sw128(A_hi + s * TC_ATILE + kk * 32), bd, idesc, (kt > kt0) || kk != 0);
                                 mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                             }
                         }
@@ -676,6 +691,10 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const int p = mt * TC_TILE_M + quarter * 32 + lane;
             const uint32_t lanes = uint32_t(quarter * 32) << 16;
             const float inv_s = p < nh ? float(1.0 / a.sinth[p]) : 0.f;
+            // a parity whose table tiles are all negligible at this latitude
+            // tile had no MMA: its accumulator holds no data and counts as 0
+            const bool zE = a.kt0[(2 * m) * a.nmt + mt] >= syn_nkt(N, m, 0);
+            const bool zO = a.kt0[(2 * m + 1) * a.nmt + mt] >= syn_nkt(N, m, 1);
             for (int q = 0; q < ngi; ++q) {
                 uint32_t e[12], o[12];
                 const uint32_t ce = tmem + lanes + uint32_t((buf * 2 + 0) * brows + 12 * q);
@@ -694,8 +713,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 tmem_wait_ld();
                 if (!ok || p >= nh || *abort) continue;
                 if (m == 1) {
-                    const float ev = __uint_as_float(pe[0]) + __uint_as_float(pe[1]);
-                    const float ov = __uint_as_float(po[0]) + __uint_as_float(po[1]);
+                    const float ev = zE ? 0.f : __uint_as_float(pe[0]) + __uint_as_float(pe[1]);
+                    const float ov = zO ? 0.f : __uint_as_float(po[0]) + __uint_as_float(po[1]);
                     float2* o0 = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
                     o0[gsyn_index(a.pairs, 2, 0, p, N, nlat)] = make_float2(ev + ov, 0.f);
                     if (nlat - 1 - p != p) o0[gsyn_index(a.pairs, 2, 0, nlat - 1 - p, N, nlat)] = make_float2(ev - ov, 0.f);
@@ -703,8 +722,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 float E[6], O[6];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    E[c] = __uint_as_float(e[c]) + __uint_as_float(e[6 + c]);
-                    O[c] = __uint_as_float(o[c]) + __uint_as_float(o[6 + c]);
+                    E[c] = zE ? 0.f : __uint_as_float(e[c]) + __uint_as_float(e[6 + c]);
+                    O[c] = zO ? 0.f : __uint_as_float(o[c]) + __uint_as_float(o[6 + c]);
                 }
                 float2* out = reinterpret_cast<float2*>(a.gsyn) + size_t(g * a.ng + q) * a.sgs;
 #pragma unroll
@@ -840,6 +859,36 @@ bool tc_supported(const sphnse_plan* P) { return P->nh % 8 == 0 && P->nh >= 16 &
 // Tensor maps over the whole [ext row][nh] bf16 tables, the analysis items
 // (128-row tiles split into groups of at most 32 / (4 NF) overlapped blocks)
 // and their LPT schedule over one CTA per SM.
+// max |Pt| of every table row over each 64-latitude chunk (once per plan,
+// from the FP64 master table [n_ext][nh])
+static const std::vector<float>& tc_chunk_max(sphnse_plan* P) {
+    auto& cm = P->tc.chunk_max;
+    const int nh = P->nh, nch = (nh + TC_TILE_K - 1) / TC_TILE_K;
+    if (cm.size() == size_t(P->n_ext) * nch) return cm;
+    cm.assign(size_t(P->n_ext) * nch, 0.f);
+    const double* t = P->psyn_host.data();
+    for (int r = 0; r < P->n_ext; ++r)
+        for (int p = 0; p < nh; ++p) {
+            float& v = cm[size_t(r) * nch + p / TC_TILE_K];
+            v = std::max(v, float(std::fabs(t[size_t(r) * nh + p])));
+        }
+    return cm;
+}
+
+// first 64-latitude chunk (from the pole) in which one of the rows
+// tile * 128 + [s, e) of the given pieces reaches TC_SKIP; at most nch - 1
+static int ana_first_chunk(const std::vector<float>& cm, int nch, int tile, const int4* pcs, int np) {
+    int c0 = nch - 1;
+    for (int j = 0; j < np; ++j)
+        for (int r = tile * TC_TILE_M + pcs[j].z; r < tile * TC_TILE_M + pcs[j].w; ++r)
+            for (int c = 0; c < c0; ++c)
+                if (cm[size_t(r) * nch + c] >= TC_SKIP) {
+                    c0 = c;
+                    break;
+                }
+    return c0;
+}
+
 int tc_setup_analysis(sphnse_plan* P, int nf) {
     if (P->tc.ana_ready && P->tc.ana_nf == nf) return SPHNSE_OK;
     EncodeTiledFn enc = encode_fn();
@@ -872,7 +921,7 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
     const int maxp = TC_ANA_BROWS / (4 * nf);
     const int ntile = (n_ext + TC_TILE_M - 1) / TC_TILE_M;
     std::vector<int4> pieces, items;
-    std::vector<int> cost;
+    std::vector<double> cost;
     {
         std::vector<std::vector<int4>> per(ntile);
         for (int m = 0; m <= N; ++m)
@@ -885,17 +934,20 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
                     r = end;
                 }
             }
+        const auto& cm = tc_chunk_max(P);
+        const int nch = (nh + TC_TILE_K - 1) / TC_TILE_K;
         for (int tt = 0; tt < ntile; ++tt)
             for (size_t j0 = 0; j0 < per[tt].size(); j0 += maxp) {
                 const int np = int(std::min<size_t>(maxp, per[tt].size() - j0));
                 const int ncol = ((4 * nf * np + 15) / 16) * 16;
-                items.push_back(make_int4(tt, int(pieces.size()), np, ncol));
+                const int kt0 = ana_first_chunk(cm, nch, tt, per[tt].data() + j0, np);
+                items.push_back(make_int4(tt, int(pieces.size()), np, ncol | (kt0 << 16)));
                 int rows = 0;
                 for (int j = 0; j < np; ++j) {
                     pieces.push_back(per[tt][j0 + j]);
                     rows += per[tt][j0 + j].w - per[tt][j0 + j].z;
                 }
-                cost.push_back(TC_TILE_M + 24 * np);
+                cost.push_back((TC_TILE_M + 24 * np) * double(nch - kt0) / nch);
                 (void)rows;
             }
     }
@@ -905,7 +957,7 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     const int G = std::min<int>(P->n_cta, int(items.size()));
     std::vector<std::vector<int4>> bins(G);
-    std::vector<long> load(G, 0);
+    std::vector<double> load(G, 0.0);
     for (int idx : order) {
         int b = int(std::min_element(load.begin(), load.end()) - load.begin());
         bins[b].push_back(items[idx]);
@@ -1036,6 +1088,31 @@ int tc_setup_synthesis(sphnse_plan* P) {
         cudaMemcpy(T.tile_info, ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice);
         T.ntiles = int(ti.size());
     }
+    {   // first significant K tile of every (block, latitude tile)
+        const auto& cm = tc_chunk_max(P);
+        const int nch = (nh + TC_TILE_K - 1) / TC_TILE_K, nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
+        std::vector<int> k0(size_t(nblk) * nmt);
+        for (int b = 0; b < nblk; ++b) {
+            const int m = b / 2, par = b % 2;
+            const int n = par ? ext_odd(N, m) : ext_even(N, m);
+            const int r0 = ext_off(N, m) + (par ? ext_even(N, m) : 0), nkt = syn_nkt(N, m, par);
+            for (int mt = 0; mt < nmt; ++mt) {
+                int kt0 = nkt;   // nkt: the whole block is negligible on this latitude tile
+                for (int j = 0; j < n && j / TC_TILE_K < kt0; ++j) {
+                    const size_t r = size_t(r0 + j) * nch;
+                    float v = cm[r + 2 * mt];
+                    if (2 * mt + 1 < nch) v = std::max(v, cm[r + 2 * mt + 1]);
+                    if (v >= TC_SKIP) kt0 = std::min(kt0, j / TC_TILE_K);
+                }
+                k0[size_t(b) * nmt + mt] = kt0;
+            }
+        }
+        if (cudaMalloc(reinterpret_cast<void**>(&T.syn_kt0), k0.size() * sizeof(int)) != cudaSuccess)
+            return SPHNSE_E_NOMEM;
+        cudaMemcpy(T.syn_kt0, k0.data(), k0.size() * sizeof(int), cudaMemcpyHostToDevice);
+        T.syn_nmt = nmt;
+        T.syn_kt0_host = k0;
+    }
     T.tsyn_bytes = 2 * total * 2;
     T.syn_ready = true;
     const int rc = tc_batch_init(P, 1, &T.single);
@@ -1072,7 +1149,10 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
             for (int mt = 0; mt < nmt; ++mt) {
                 its.push_back(make_int4(m, mt, g, 0));
                 // streamed stages (A and B bytes) plus a fixed cost per item and the epilogue of the group
-                cost.push_back((syn_nkt(N, m, 0) + syn_nkt(N, m, 1)) * (1.0 + T.brows / 256.0) + 1.0 + 0.1 * (ngi - 1));
+                const auto& k0 = P->tc.syn_kt0_host;
+                const int nst = syn_nkt(N, m, 0) - k0[size_t(2 * m) * nmt + mt] + syn_nkt(N, m, 1) -
+                                k0[size_t(2 * m + 1) * nmt + mt];
+                cost.push_back(nst * (1.0 + T.brows / 256.0) + 1.0 + 0.1 * (ngi - 1));
             }
     }
     std::vector<int> order(its.size());
@@ -1131,7 +1211,7 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
                 reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
                 P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
-                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2};
+                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2, P->tc.syn_kt0, P->tc.syn_nmt};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     const cudaError_t e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
@@ -1178,6 +1258,7 @@ int tc_batch_ana_init(sphnse_plan* P, int nb, TcBatchA* B) {
     T.nb = nb;
     T.nkt = (nh + TC_TILE_K - 1) / TC_TILE_K;
     const auto per = tile_pieces(N, P->n_ext);
+    const auto& cm = tc_chunk_max(P);
     std::vector<int4> items, slots;
     std::vector<double> cost;
     for (int tt = 0; tt < int(per.size()); ++tt) {
@@ -1194,8 +1275,9 @@ int tc_batch_ana_init(sphnse_plan* P, int nb, TcBatchA* B) {
                         slots.push_back(make_int4(pc.x, pc.y, k, pc.z | (pc.w << 16)));
                     }
                 const int ns = int(slots.size()) - first;
-                items.push_back(make_int4(tt, first, ns, ((8 * ns + 15) / 16) * 16));
-                cost.push_back(T.nkt * (1.0 + ns / 32.0) + 0.2 * ns);
+                const int kt0 = ana_first_chunk(cm, T.nkt, tt, per[tt].data() + j0, jn);
+                items.push_back(make_int4(tt, first, ns, ((8 * ns + 15) / 16) * 16 | (kt0 << 16)));
+                cost.push_back((T.nkt - kt0) * (1.0 + ns / 32.0) + 0.2 * ns);
             }
     }
     std::vector<int> order(items.size());
@@ -1260,7 +1342,7 @@ int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gan
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
     void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
-                    T.tsyn_lo, T.tile_off, T.tile_info};
+                    T.tsyn_lo, T.tile_off, T.tile_info, T.syn_kt0};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     tc_batch_free(&T.single);
