@@ -150,6 +150,31 @@ int sphnse_grid_fields(sphnse_plan* plan, const double* alpha, double* zeta,
  * v_theta, v_phi: (device) [nlat][nlon]; out: (device) packed. */
 int sphnse_project(sphnse_plan* plan, const double* v_theta, const double* v_phi, double* out);
 
+/* ---- diagnostics (Sec. 6.2) --------------------------------------------- */
+
+/* Energy spectrum E(L) = sum_{|m| <= L} |alpha_{L,m}|^2, Eq. (energy), for
+ * L = 0..N (E(0) = 0; an order m > 0 counts twice, for m and -m).
+ * alpha: (device) packed; E: (device) N + 1 doubles.  Deterministic: a fixed
+ * summation order per degree. */
+int sphnse_energy_spectrum(sphnse_plan* plan, const double* alpha, double* E);
+
+/* The field alpha_in of truncation N_in in the packed layout of the plan's
+ * truncation N: modes with L <= min(N_in, N, L_max) copied, all others zero
+ * (L_max < 0: no extra cut).  With L_max = N1 this is the projection P_{N1}
+ * of Eq. (eq: cut_app_soln).  alpha_in, alpha_out: (device), not
+ * overlapping. */
+int sphnse_resize(sphnse_plan* plan, int N_in, const double* alpha_in, int L_max, double* alpha_out);
+
+/* Approximate inertial manifold of Eq. (eq:p-p) on a plan of truncation
+ * N2 = N > N1: phi = (nu A + C)^{-1} (P_{N2} - P_{N1}) [f - B(u1, u1)] with
+ * u1 = P_{N1} alpha, i.e. the RHS of Eq. (ode) at u1 divided by
+ * nu lambda_L - 2 i Omega m / lambda_L for N1 < L <= N2, and 0 for L <= N1.
+ * alpha, forcing (nullable), phi: (device) packed, degree N2.  Uses the
+ * plan's step workspace as scratch (do not call it inside a step).
+ * E_ARG unless 1 <= N1 < N and nu > 0. */
+int sphnse_inertial_manifold(sphnse_plan* plan, int N1, const double* alpha, const double* forcing,
+                             double* phi);
+
 /* ---- adaptive NDF time step (Sec. 4.2, Eq. (ode_disc)) ------------------ */
 
 typedef struct {

@@ -135,6 +135,38 @@ class Plan:
         check("sphnse_project", _capi.lib().sphnse_project(self._h, _ptr(v_theta), _ptr(v_phi), _ptr(out)))
         return out
 
+    # -- diagnostics (Sec. 6.2) -------------------------------------------
+    def energy_spectrum(self, alpha):
+        """E(L), L = 0..L_plan, of Eq. (energy): float64 CUDA tensor."""
+        torch = _torch()
+        alpha = self._coeff(alpha, "alpha")
+        E = torch.empty(self.L + 1, dtype=torch.float64, device=self.device)
+        self._stream()
+        check("sphnse_energy_spectrum", _capi.lib().sphnse_energy_spectrum(self._h, _ptr(alpha), _ptr(E)))
+        return E
+
+    def resize(self, alpha_in, N_in, L_max=-1, out=None):
+        """A field of truncation N_in in this plan's layout (modes above
+        min(N_in, N, L_max) zero); L_max = N1 gives P_{N1}."""
+        torch = _torch()
+        if alpha_in.dtype != torch.complex128 or not alpha_in.is_cuda or not alpha_in.is_contiguous() \
+                or alpha_in.numel() != (N_in + 1) * (N_in + 2) // 2 - 1:
+            raise ValueError("alpha_in must be a packed complex128 CUDA tensor of truncation N_in")
+        out = self.empty_coeff() if out is None else self._coeff(out, "out")
+        self._stream()
+        check("sphnse_resize", _capi.lib().sphnse_resize(self._h, int(N_in), _ptr(alpha_in), int(L_max), _ptr(out)))
+        return out
+
+    def inertial_manifold(self, N1, alpha, forcing=None, out=None):
+        """Phi(P_{N1} alpha) of Eq. (eq:p-p) with N2 = this plan's N."""
+        alpha = self._coeff(alpha, "alpha")
+        forcing = self._coeff(forcing, "forcing")
+        out = self.empty_coeff() if out is None else self._coeff(out, "out")
+        self._stream()
+        check("sphnse_inertial_manifold", _capi.lib().sphnse_inertial_manifold(
+            self._h, int(N1), _ptr(alpha), _ptr(forcing), _ptr(out)))
+        return out
+
     # -- adjoint ----------------------------------------------------------
     def rhs_adjoint(self, alpha, w, out=None, want_nu=False):
         """J(alpha)^T w (packed real components); with want_nu also <w, dF/dnu>."""

@@ -72,6 +72,10 @@ _SIGS = {
     "sphnse_ensemble_rhs": (ctypes.c_int, [ctypes.c_void_p]),
     "sphnse_ensemble_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "sphnse_ensemble_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sphnse_energy_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sphnse_resize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sphnse_inertial_manifold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
     "sphnse_ensemble_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sphnse_stage_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sphnse_stage_times": (ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.POINTER(ctypes.c_long)]),
