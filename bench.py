@@ -104,9 +104,13 @@ def sizes(L, nlat):
     return nh, n_ext, nh * n_ext
 
 
-def algorithmic(stage, L, nlat, prec):
-    """(bytes, flops) one launch of a stage must move / execute at minimum."""
+def algorithmic(stage, L, nlat, prec, entries=None):
+    """(bytes, flops) one launch of a stage must move / execute at minimum.
+    entries: table entries the kernel reads when it skips tiles of negligible
+    entries (the tensor-core path), else every entry E."""
     nh, n_ext, E = sizes(L, nlat)
+    if entries:
+        E = int(entries)
     tb = {"fp64": 8, "fp32": 4, "bf16x3": 4}[prec]     # table bytes per entry (hi+lo for bf16)
     vb = 8 if prec == "fp64" else 4                     # intermediate real size
     g = nlat * (L + 1) * 2 * vb                         # one complex [nlat][L+1] field
@@ -501,11 +505,15 @@ def main():
 
     # dominant kernel and its roofline (live durations from the timed region)
     avg_ms = stage[dom]["ms"] / max(stage[dom]["launches"], 1)
-    nbytes, _ = algorithmic(dom, L, nlat, prec)
+    ent = None
+    if prec == "bf16x3" and dom in ("synthesis", "analysis"):
+        ent = plan.get("SYN_ENTRIES" if dom == "synthesis" else "ANA_ENTRIES")
+    nbytes, _ = algorithmic(dom, L, nlat, prec, ent)
     peak, peak_kind = peaks()
     achieved = nbytes / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes": nbytes,
+                "table_entries": ent if ent else sizes(L, nlat)[2],
                 "avg_launch_ms": avg_ms, "timed_launches": stage[dom]["launches"],
                 "duration_sampling": f"CUDA events around every {SAMPLE}th launch in the timed region",
                 "traffic": ncu_traffic(f"{dom}:{prec}:L511")}

@@ -79,6 +79,10 @@ extern "C" {
 #define SPHNSE_KEY_TABLE_BYTES   104  /* read-only: device bytes of Legendre tables held */
 #define SPHNSE_KEY_ROUNDS        105  /* read-only (ensemble): graph launches (rounds) of the
                                          last sphnse_ensemble_advance / _step call */
+#define SPHNSE_KEY_SYN_ENTRIES   106  /* read-only: table entries Pt_K^m(x_p) one tensor-core
+                                         synthesis reads (tiles of negligible entries
+                                         excluded; 0 before the BF16X3 tables exist) */
+#define SPHNSE_KEY_ANA_ENTRIES   107  /* read-only: the same for the tensor-core analysis */
 
 #define SPHNSE_FP64    0  /* FP64 tables and arithmetic throughout */
 #define SPHNSE_FP32    1  /* FP32 tables, contractions, FFTs; FP64 state and update */

@@ -133,6 +133,7 @@ struct TcState {
     // (table row, 64-latitude chunk)
     int* syn_kt0 = nullptr;
     int syn_nmt = 0;
+    double syn_entries = 0, ana_entries = 0;   // table entries one launch reads (skip rule applied)
     std::vector<int> syn_kt0_host;
     std::vector<float> chunk_max;
 };

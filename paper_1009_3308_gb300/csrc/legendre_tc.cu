@@ -902,6 +902,7 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
     T.ana_off = nullptr;
     T.ana_pieces = nullptr;
     T.ana_ready = false;
+    T.ana_entries = 0;
     const Tables& t = P->tab[SPHNSE_BF16X3];
     const int N = P->N, nh = P->nh, n_ext = P->n_ext;
     CUtensorMap mh, ml;
@@ -942,6 +943,8 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
                 const int ncol = ((4 * nf * np + 15) / 16) * 16;
                 const int kt0 = ana_first_chunk(cm, nch, tt, per[tt].data() + j0, np);
                 items.push_back(make_int4(tt, int(pieces.size()), np, ncol | (kt0 << 16)));
+                for (size_t j = j0; j < j0 + np; ++j)
+                    T.ana_entries += double(per[tt][j].w - per[tt][j].z) * (nh - std::min(nh, kt0 * TC_TILE_K));
                 int rows = 0;
                 for (int j = 0; j < np; ++j) {
                     pieces.push_back(per[tt][j0 + j]);
@@ -1088,6 +1091,7 @@ int tc_setup_synthesis(sphnse_plan* P) {
         cudaMemcpy(T.tile_info, ti.data(), ti.size() * sizeof(int2), cudaMemcpyHostToDevice);
         T.ntiles = int(ti.size());
     }
+    T.syn_entries = 0;
     {   // first significant K tile of every (block, latitude tile)
         const auto& cm = tc_chunk_max(P);
         const int nch = (nh + TC_TILE_K - 1) / TC_TILE_K, nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
@@ -1105,6 +1109,9 @@ int tc_setup_synthesis(sphnse_plan* P) {
                     if (v >= TC_SKIP) kt0 = std::min(kt0, j / TC_TILE_K);
                 }
                 k0[size_t(b) * nmt + mt] = kt0;
+                const int rows = std::min(nh, (mt + 1) * TC_TILE_M) - mt * TC_TILE_M;
+                for (int kt = kt0; kt < nkt; ++kt)
+                    T.syn_entries += double(rows) * std::min(TC_TILE_K, n - kt * TC_TILE_K);
             }
         }
         if (cudaMalloc(reinterpret_cast<void**>(&T.syn_kt0), k0.size() * sizeof(int)) != cudaSuccess)

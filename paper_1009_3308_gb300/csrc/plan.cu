@@ -433,6 +433,8 @@ int sphnse_plan_get(const sphnse_plan* P, int key, double* v) {
         case SPHNSE_KEY_L: *v = P->N; break;
         case SPHNSE_KEY_NLAT: *v = P->nlat; break;
         case SPHNSE_KEY_NLON: *v = P->nlon; break;
+        case SPHNSE_KEY_SYN_ENTRIES: *v = P->tc.syn_entries; break;
+        case SPHNSE_KEY_ANA_ENTRIES: *v = P->tc.ana_entries; break;
         case SPHNSE_KEY_TABLE_BYTES: {
             double b = double(P->tc.tsyn_bytes);
             for (const auto& t : P->tab) b += double(t.bytes);
