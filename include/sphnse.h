@@ -142,6 +142,22 @@ int sphnse_grid_nodes(const sphnse_plan* plan, double* theta, double* x, double*
 int sphnse_rhs(sphnse_plan* plan, double t, const double* alpha, const double* forcing,
                double* dalpha_dt);
 
+/* F(t, alpha) of Eq. (ode) from HOST arrays, pipelined across calls.  Each
+ * call copies alpha_h (and forcing_h, nullable) into one of two plan-owned
+ * device staging slots on an upload stream, evaluates F on the plan's stream
+ * and copies it to out_h on a download stream, and returns without waiting
+ * (*ticket, nullable, numbers the call from 0).  Call k + 1's upload overlaps
+ * call k's RHS and call k's download overlaps call k + 1's RHS.  The host
+ * arrays (n_coeff complex128 each; page-locked for the copies to overlap)
+ * must stay valid, and alpha_h / forcing_h unmodified, until
+ * sphnse_host_wait(plan, ticket) has returned; out_h is valid from then on. */
+int sphnse_rhs_host(sphnse_plan* plan, double t, const double* alpha_h, const double* forcing_h,
+                    double* out_h, long long* ticket);
+
+/* Block until call `ticket` of sphnse_rhs_host has copied F to the host
+ * (E_ARG for a ticket not yet issued). */
+int sphnse_host_wait(sphnse_plan* plan, long long ticket);
+
 /* Grid values of zeta = xhat.Curl_n u (Eq. (vort_app)), u_theta and u_phi
  * for the field with coefficients alpha (Eq. (app_soln_rep)).
  * alpha: (device) packed; zeta, u_theta, u_phi: (device) [nlat][nlon] doubles,

@@ -116,6 +116,25 @@ class Plan:
         check("sphnse_rhs", _capi.lib().sphnse_rhs(self._h, float(t), _ptr(alpha), _ptr(forcing), _ptr(out)))
         return out
 
+    def rhs_host(self, alpha_h, out_h, forcing_h=None, t=0.0):
+        """Pipelined F(alpha) from host tensors (complex128, pinned for
+        overlap): returns a ticket; out_h is valid after host_wait(ticket).
+        The arrays must stay alive and alpha_h / forcing_h unmodified until then."""
+        torch = _torch()
+        for name, a in (("alpha_h", alpha_h), ("out_h", out_h), ("forcing_h", forcing_h)):
+            if a is None:
+                continue
+            if a.dtype != torch.complex128 or a.is_cuda or not a.is_contiguous() or a.numel() != self.n_coeff:
+                raise ValueError(f"{name} must be a contiguous complex128 host tensor of {self.n_coeff} entries")
+        tk = ctypes.c_longlong()
+        self._stream()
+        check("sphnse_rhs_host", _capi.lib().sphnse_rhs_host(self._h, float(t), _ptr(alpha_h), _ptr(forcing_h),
+                                                             _ptr(out_h), ctypes.byref(tk)))
+        return tk.value
+
+    def host_wait(self, ticket):
+        check("sphnse_host_wait", _capi.lib().sphnse_host_wait(self._h, int(ticket)))
+
     def grid_fields(self, alpha):
         """(zeta, u_theta, u_phi) on the grid, float64 [nlat, nlon] CUDA tensors."""
         torch = _torch()

@@ -73,6 +73,9 @@ _SIGS = {
     "sphnse_ensemble_rhs": (ctypes.c_int, [ctypes.c_void_p]),
     "sphnse_ensemble_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "sphnse_ensemble_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sphnse_rhs_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "sphnse_host_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "sphnse_energy_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sphnse_resize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sphnse_inertial_manifold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,

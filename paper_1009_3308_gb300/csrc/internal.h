@@ -109,6 +109,17 @@ struct TcBatchA {
 };
 
 // tcgen05 path state (tensor maps and item schedules, built on first use)
+// staging of sphnse_rhs_host: two slots, an upload and a download stream
+struct HostIO {
+    void* din[2] = {nullptr, nullptr};
+    void* dfo[2] = {nullptr, nullptr};
+    void* dout[2] = {nullptr, nullptr};
+    cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_rhs[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+    cudaStream_t up = nullptr, down = nullptr;
+    long long calls = 0;
+    bool ready = false;
+};
+
 struct TcState {
     void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
     void* map_lo = nullptr;
@@ -198,6 +209,7 @@ struct sphnse_plan {
     long stage_calls[8] = {};    // launches seen per stage while timed
     bool stage_rec[8] = {};      // the current launch of the stage is recorded
     std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];
+    sph::HostIO hio;
     int ev_used[SPHNSE_NSTAGES] = {0};
     double stage_ms[SPHNSE_NSTAGES] = {0};
     long stage_n[SPHNSE_NSTAGES] = {0};
@@ -256,6 +268,7 @@ int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* it
 int launch_finish32_batch(sphnse_plan* P, int nb, const float* hana, size_t hstride, const double* alpha,
                           double* out, const double* nu_inst);
 void tc_free(sphnse_plan* P);
+void host_io_free(sphnse_plan* P);
 int launch_analysis_stream(sphnse_plan* P, int nfields, int prec);
 void stage_begin(sphnse_plan* P, int stage);
 void stage_end(sphnse_plan* P, int stage);

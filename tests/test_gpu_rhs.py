@@ -144,3 +144,19 @@ def test_plan_argument_errors():
     plan = _plan(7, 24, 1e-2, 1.0)
     with pytest.raises(ValueError):
         plan.rhs(torch.zeros(5, dtype=torch.complex128, device="cuda"))
+
+
+def test_rhs_host_pipelined_matches_device_rhs():
+    """sphnse_rhs_host: five pipelined calls with different host inputs (two
+    staging slots reused) give exactly the device-buffer RHS of each input."""
+    from paper_1009_3308_gb300 import Plan
+    L, nlon = 63, 192
+    plan = Plan(L, nlon // 2, nlon, 1e-3, 1.0, precision="fp32")
+    ins = [torch.from_numpy(coefficients(L, 70 + i, 0.05)).pin_memory() for i in range(5)]
+    f = torch.from_numpy(coefficients(L, 80, 0.3)).pin_memory()
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    tks = [plan.rhs_host(x, o, forcing_h=f) for x, o in zip(ins, outs)]
+    plan.host_wait(tks[-1])
+    for x, o in zip(ins, outs):
+        ref = plan.rhs(x.cuda(), forcing=f.cuda()).cpu()
+        assert torch.equal(o, ref)
