@@ -307,40 +307,63 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
 // brings A_hi, A_lo by TMA and the slots' S tiles by bulk copy into rows
 // 8 slot .. 8 slot + 7 of B, so one MMA (N = 8 slots) serves every slot.
 
+// Thread = (instance, order m, K tile, chunk q of 8 latitudes, field f): it
+// reads the 8 northern latitudes and their mirrors with 16-byte loads and
+// writes both parities' tiles, S = G(p) + G(p') to block 2m and G(p) - G(p')
+// to block 2m + 1; consecutive threads take consecutive latitude chunks.
 __global__ void __launch_bounds__(128) k_ana_prep(const float* __restrict__ gana, size_t sa, unsigned char* __restrict__ stiles,
                                                   int N, int nh, int nlat, int nkt) {
     pdl_launch();
     pdl_wait();
     const int inst = blockIdx.y;
     const int nblk = 2 * (N + 1);
-    const int t = blockIdx.x * 128 + threadIdx.x;   // (block, kt, q, f)
-    if (t >= nblk * nkt * 16) return;
-    const int f = t & 1, q = (t >> 1) & 7, kt = (t >> 4) % nkt, b = (t >> 4) / nkt;
-    const int m = b >> 1, par = b & 1;
+    const int t = blockIdx.x * 128 + threadIdx.x;   // (m, kt, f, q)
+    if (t >= (N + 1) * nkt * 16) return;
+    const int q = t & 7, f = (t >> 3) & 1, kt = (t >> 4) % nkt, m = (t >> 4) / nkt;
     const float* g = gana + size_t(inst) * sa + (size_t(f) * (N + 1) + m) * size_t(nlat) * 2;
     const int p0 = kt * TC_TILE_K + q * 8;
-    float re[8], im[8];
+    float nv[16], sv[16];
+    if (p0 + 8 <= nh) {
+        const float4* gn = reinterpret_cast<const float4*>(g + size_t(p0) * 2);
+        const float4* gs = reinterpret_cast<const float4*>(g + size_t(nlat - 8 - p0) * 2);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 x = __ldcs(gn + u), y = __ldcs(gs + u);
+            nv[4 * u] = x.x; nv[4 * u + 1] = x.y; nv[4 * u + 2] = x.z; nv[4 * u + 3] = x.w;
+            sv[4 * u] = y.x; sv[4 * u + 1] = y.y; sv[4 * u + 2] = y.z; sv[4 * u + 3] = y.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int p = p0 + e, pr = nlat - 8 - p0 + e;
+            const bool in = p < nh;
+            nv[2 * e] = in ? g[2 * size_t(p)] : 0.f;
+            nv[2 * e + 1] = in ? g[2 * size_t(p) + 1] : 0.f;
+            const bool ins = (nlat - 1 - pr) < nh && pr >= 0;
+            sv[2 * e] = ins ? g[2 * size_t(pr)] : 0.f;
+            sv[2 * e + 1] = ins ? g[2 * size_t(pr) + 1] : 0.f;
+        }
+    }
+    // latitude p0 + e pairs with its mirror nlat - 1 - p0 - e = sv entry 7 - e
+    float er[8], ei[8], odr[8], odi[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int p = p0 + e;
-        float nr = 0.f, ni = 0.f, sr = 0.f, si = 0.f;
-        if (p < nh) {
-            nr = g[2 * size_t(p)];
-            ni = g[2 * size_t(p) + 1];
-            const int pr = nlat - 1 - p;
-            if (pr != p) {
-                sr = g[2 * size_t(pr)];
-                si = g[2 * size_t(pr) + 1];
-            }
-        }
-        re[e] = par ? nr - sr : nr + sr;
-        im[e] = par ? ni - si : ni + si;
+        const float sr = sv[2 * (7 - e)], si = sv[2 * (7 - e) + 1];
+        er[e] = nv[2 * e] + sr;
+        ei[e] = nv[2 * e + 1] + si;
+        odr[e] = nv[2 * e] - sr;
+        odi[e] = nv[2 * e + 1] - si;
     }
-    unsigned char* tile = stiles + ((size_t(inst) * nblk + b) * nkt + kt) * 1024;
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f, q)) = pack_hi(re);
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(2 * f + 1, q)) = pack_hi(im);
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(4 + 2 * f, q)) = pack_lo(re);
-    *reinterpret_cast<uint4*>(tile + sw128_chunk(5 + 2 * f, q)) = pack_lo(im);
+    unsigned char* te = stiles + ((size_t(inst) * nblk + 2 * m) * nkt + kt) * 1024;
+    unsigned char* to = te + size_t(nkt) * 1024;
+    *reinterpret_cast<uint4*>(te + sw128_chunk(2 * f, q)) = pack_hi(er);
+    *reinterpret_cast<uint4*>(te + sw128_chunk(2 * f + 1, q)) = pack_hi(ei);
+    *reinterpret_cast<uint4*>(te + sw128_chunk(4 + 2 * f, q)) = pack_lo(er);
+    *reinterpret_cast<uint4*>(te + sw128_chunk(5 + 2 * f, q)) = pack_lo(ei);
+    *reinterpret_cast<uint4*>(to + sw128_chunk(2 * f, q)) = pack_hi(odr);
+    *reinterpret_cast<uint4*>(to + sw128_chunk(2 * f + 1, q)) = pack_hi(odi);
+    *reinterpret_cast<uint4*>(to + sw128_chunk(4 + 2 * f, q)) = pack_lo(odr);
+    *reinterpret_cast<uint4*>(to + sw128_chunk(5 + 2 * f, q)) = pack_lo(odi);
 }
 
 struct TcAnaBArgs {
@@ -402,8 +425,11 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
         // lane 0 waits for the slot and posts the byte count; every lane then
         // issues the bulk copy of one slot's S tile (lane 0 also the A tiles)
         pdl_wait();
-        const uint64_t pol = policy_evict_first();
-        const uint64_t polb = policy_evict_last();
+        // the table tile is read again by the tile's other instance items (an
+        // ensemble bucket's table is a few MB): keep it in L2; the S tiles are
+        // read once
+        const uint64_t pol = policy_evict_last();
+        const uint64_t polb = policy_evict_first();
         int it = 0;
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
@@ -596,8 +622,10 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         if (lane == 0) {
             // the table tiles of the first ns stages do not depend on the
             // predecessor (the B tiles do): they are requested before the wait,
-            // overlapping the coefficient prep, and their B tiles right after it
-            const uint64_t pol = policy_evict_first();
+            // overlapping the coefficient prep, and their B tiles right after it.
+            // One group streams the table once (evict-first); several groups
+            // re-read it (an ensemble bucket's table: a few MB), so it stays.
+            const uint64_t pol = a.nb > a.ng ? policy_evict_last() : policy_evict_first();
             const uint64_t polb = policy_evict_last();
             const unsigned char* pend[NS];
             bool waited = false;
@@ -1329,11 +1357,10 @@ void tc_batch_ana_free(TcBatchA* B) {
 
 int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gana, size_t sa_floats, float* hana,
                              size_t sh_floats) {
-    const int nblk = 2 * (P->N + 1);
     const size_t sm = 1024 + size_t(TC_ANAB_NS) * (2 * size_t(TC_ATILE) + TC_ANAB_BBYTES) + 512;
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
-    cudaError_t e = launch_pdl(k_ana_prep, dim3((nblk * B.nkt * 16 + 127) / 128, B.nb), dim3(128), 0, P->stream, gana,
+    cudaError_t e = launch_pdl(k_ana_prep, dim3(((P->N + 1) * B.nkt * 16 + 127) / 128, B.nb), dim3(128), 0, P->stream, gana,
                                sa_floats, B.stiles, P->N, P->nh, P->nlat, B.nkt);
     if (e == cudaSuccess) {
         cudaFuncSetAttribute(k_ana_tc_b, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
