@@ -310,8 +310,31 @@ def extra_L31(torch, nsteps=100):
     integ = Integrator(plan, torch.from_numpy(w["alpha0"]).cuda(), forcing=torch.from_numpy(w["forcing"]).cuda())
     infos, el = _timed(lambda: [integ.step() for _ in range(nsteps)], torch)
     rhs = sum(i["rhs_evals"] for i in infos)
+    # latency-bound: one RHS back to back and with a host round trip, next to
+    # the floor of one tiny kernel launch + synchronize on this stream
+    a = torch.from_numpy(w["alpha0"]).cuda()
+    out = plan.empty_coeff()
+    ms_b2b = time_rhs(plan, a, out, 2000, torch)
+    lat = []
+    for _ in range(200):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.rhs(a, out=out)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    x = torch.zeros(1, device="cuda")
+    floor = []
+    for _ in range(200):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.add_(1.0)
+        torch.cuda.synchronize()
+        floor.append(time.perf_counter() - t0)
+    lat.sort()
+    floor.sort()
     return {"steps_per_s": nsteps / el, "rhs_per_s": rhs / el, "steps": nsteps, "t_reached": integ.t,
-            "precision": "fp64"}
+            "precision": "fp64", "rhs_us_back_to_back": 1e3 * ms_b2b, "rhs_us_with_sync_median": 1e6 * lat[100],
+            "launch_sync_floor_us_median": 1e6 * floor[100]}
 
 
 def extra_adjoint(torch, nsteps=200, checkpoint=20):

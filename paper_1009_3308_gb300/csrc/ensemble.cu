@@ -113,21 +113,30 @@ __global__ void kb_rescale(const int2* btab, const InstPar* par, double2* dif) {
 }
 
 __global__ void kb_predict(const int2* btab, const InstPar* par, const double2* y, const double2* dif, double2* y0,
-                           double2* psi, double2* d, double2* ynew) {
-    INST_PROLOGUE(F_PREDICT)
-    const double2* D = dif + 7 * o;
-    double2 a = y[o + i], q = make_double2(0.0, 0.0);
-    for (int j = 0; j < p.k; ++j) {
-        const double2 dj = D[size_t(j) * p.n + i];
-        a.x += dj.x;
-        a.y += dj.y;
-        q.x += p.g[j] * dj.x;
-        q.y += p.g[j] * dj.y;
+                           double2* psi, double2* d, double2* ynew, unsigned long long* norms) {
+    INST_PROLOGUE_ALL(F_PREDICT)
+    float r[1] = {0.f};
+    if (i < p.n) {
+        const double2* D = dif + 7 * o;
+        const double2 yi = y[o + i];
+        double2 a = yi, q = make_double2(0.0, 0.0);
+        for (int j = 0; j < p.k; ++j) {
+            const double2 dj = D[size_t(j) * p.n + i];
+            a.x += dj.x;
+            a.y += dj.y;
+            q.x += p.g[j] * dj.x;
+            q.y += p.g[j] * dj.y;
+        }
+        y0[o + i] = a;
+        ynew[o + i] = a;
+        psi[o + i] = q;
+        d[o + i] = make_double2(0.0, 0.0);
+        // slot 4: ||y / max(|y|, thr)||_inf (FP32, as the corrector's norms)
+        const float thr = fmaxf(float(p.thr), 1e-30f), ax = absf_trunc(yi.x), ay = absf_trunc(yi.y);
+        r[0] = fmaxf(ax / fmaxf(ax, thr), ay / fmaxf(ay, thr));
     }
-    y0[o + i] = a;
-    ynew[o + i] = a;
-    psi[o + i] = q;
-    d[o + i] = make_double2(0.0, 0.0);
+    const int id[1] = {4};
+    block_amax_f<1>(norms + 8 * bt.x, r, id, false);
 }
 
 __global__ void kb_newton(const int2* btab, const InstPar* par, const double2* F, const double2* y,
@@ -686,8 +695,8 @@ static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_in
         if (cudaMemsetAsync(E->d_norms, 0, nb, st) != cudaSuccess) return SPHNSE_E_CUDA;
         kb_accept<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
         kb_rescale<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif);
-        kb_predict<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew);
-        kb_wnorm<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, F_PREDICT, E->alpha, E->alpha, E->d_norms, 4);
+        kb_predict<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew,
+                                           E->d_norms);
         int r = batched_rhs(E, E->ynew, E->F);
         if (r) return r;
         kb_newton<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->F, E->alpha, E->y0, E->psi, E->d, E->ynew,

@@ -121,22 +121,31 @@ __global__ void k_rescale(double2* dif, Mat A, int k, int n) {
 }
 
 // y0 = y + sum_{j<k} D_j,  psi = sum_{j<k} g_j D_j,  d = 0,  ynew = y0
+// and slot 4 = ||y / max(|y|, thr)||_inf, the scale of the corrector's
+// rounding-level stop (FP32, like the corrector's other norms)
 __global__ void k_predict(const double2* y, const double2* dif, Coef g, int k, double2* y0, double2* psi,
-                          double2* d, double2* ynew, int n) {
+                          double2* d, double2* ynew, float thr, unsigned long long* slots, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double2 a = y[i], p = make_double2(0.0, 0.0);
-    for (int j = 0; j < k; ++j) {
-        const double2 dj = dif[size_t(j) * n + i];
-        a.x += dj.x;
-        a.y += dj.y;
-        p.x += g.c[j] * dj.x;
-        p.y += g.c[j] * dj.y;
+    float r[1] = {0.f};
+    if (i < n) {
+        const double2 yi = y[i];
+        double2 a = yi, p = make_double2(0.0, 0.0);
+        for (int j = 0; j < k; ++j) {
+            const double2 dj = dif[size_t(j) * n + i];
+            a.x += dj.x;
+            a.y += dj.y;
+            p.x += g.c[j] * dj.x;
+            p.y += g.c[j] * dj.y;
+        }
+        y0[i] = a;
+        ynew[i] = a;
+        psi[i] = p;
+        d[i] = make_double2(0.0, 0.0);
+        const float ax = absf_trunc(yi.x), ay = absf_trunc(yi.y);
+        r[0] = fmaxf(ax / fmaxf(ax, thr), ay / fmaxf(ay, thr));
     }
-    y0[i] = a;
-    ynew[i] = a;
-    psi[i] = p;
-    d[i] = make_double2(0.0, 0.0);
+    const int id[1] = {4};
+    block_amax_f<1>(slots, r, id, false);
 }
 
 // One simplified-Newton update: r = c F - (psi + d), dl = r / (1 - c J_d),
@@ -444,14 +453,12 @@ int corrector(sphnse_plan* P, sphnse_state* st, const double* forcing, double h,
     Coef g;
     for (int j = 0; j < SPHNSE_MAXK; ++j) g.c[j] = j < k ? C.gamma[j] * C.iga[k - 1] : 0.0;
     int rc;
+    if ((rc = clear_norms(P))) return rc;
     stage_begin(P, SPHNSE_STAGE_STEP);
     k_predict<<<grid(n), 256, 0, P->stream>>>(reinterpret_cast<const double2*>(st->alpha),
                                                reinterpret_cast<const double2*>(st->dif), g, k, W.y0, W.psi, W.d,
-                                               W.ynew, n);
+                                               W.ynew, fmaxf(float(thr), 1e-30f), P->d_norms, n);
     stage_end(P, SPHNSE_STAGE_STEP);
-    if ((rc = clear_norms(P))) return rc;
-    k_wnorm<<<grid(n), 256, 0, P->stream>>>(reinterpret_cast<const double2*>(st->alpha),
-                                             reinterpret_cast<const double2*>(st->alpha), thr, P->d_norms, 4, n);
     if ((rc = stage_launch_check(P))) return rc;
     const double cc = h * C.iga[k - 1];
     const double eps = 2.220446049250313e-16;
