@@ -137,3 +137,32 @@ def test_state_after_500_replayed_steps_bf16x3_vs_fp64():
     print(f"500 replayed steps: bf16x3 vs fp64 state rel err {err:.3e} (adaptive run vs fp64 replay {drift:.3e}),"
           f" t = {sum(h for h, _ in sched):.4g}")
     assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_zero_state_gives_the_forcing_exactly(prec):
+    """Degenerate case: alpha = 0 has no nonlinear, Coriolis or viscous term,
+    so F = fhat bit for bit in every precision (L = 511 workload grid)."""
+    from paper_1009_3308_gb300 import Plan
+    w = workload("L511")
+    c = w["config"]
+    f = coefficients(c["L"], 4242, 0.02)
+    plan = Plan(c["L"], c["nlat"], c["nlon"], c["nu"], c["Omega"], precision=prec)
+    got = plan.rhs(_dev(np.zeros_like(f)), forcing=_dev(f)).cpu().numpy()
+    np.testing.assert_array_equal(got, f)
+
+
+@pytest.mark.parametrize("L,nlon", [(5, 18), (127, 768)])
+def test_bf16x3_plan_off_the_tensor_core_grid(L, nlon):
+    """A BF16X3 plan whose grid the tensor-core kernels do not take (odd
+    nlat) runs the FP32 kernels; an oversampled grid (M = 6 (N + 1)) runs the
+    tensor-core kernels with 192 northern nodes: both within the mixed bound
+    against the oracle."""
+    from paper_1009_3308_gb300 import Plan
+    prob = Problem(L, nlon, 1e-3, 1.0)
+    a = coefficients(L, 500 + L, 0.05) * 3.0
+    ref = rhs_separable(prob, a)
+    got = Plan(L, nlon // 2, nlon, 1e-3, 1.0, precision="bf16x3").rhs(_dev(a)).cpu().numpy()
+    err = _rel(got, ref)
+    print(f"L={L} nlon={nlon} bf16x3 plan rel err {err:.2e}")
+    assert err <= 3e-5, err
