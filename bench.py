@@ -298,6 +298,23 @@ def extra_coriolis_split(torch, prec):
             "rel_diff_vs_unsplit": float(np.linalg.norm(split - full) / np.linalg.norm(full))}
 
 
+def extra_batched_L511(torch, n=4, reps=200):
+    """n independent L = 511 states in one batched BF16X3 RHS (an ensemble
+    bucket): one table stream per stage serves every state of the group.
+    Context for the single-state headline, not a substitute for it."""
+    from paper_1009_3308_gb300 import Ensemble
+    from seeded_inputs import coefficients, workload
+    w = workload("L511")
+    c = w["config"]
+    ens = Ensemble([c["L"]] * n, [c["nu"]] * n, c["Omega"], precision="bf16x3")
+    for i in range(n):
+        ens.set_alpha(i, torch.from_numpy(coefficients(c["L"], 3000 + i, 0.02)))
+    for _ in range(5):
+        ens.rhs()
+    _, el = _timed(lambda: [ens.rhs() for _ in range(reps)], torch)
+    return {"states": n, "rhs_per_s": n * reps / el, "us_per_batched_rhs": 1e6 * el / reps}
+
+
 def extra_L31(torch, nsteps=100):
     """The L = 31 workload: 100 adaptive FP64 steps, rtol 1e-8, steady forcing."""
     from paper_1009_3308_gb300 import Integrator, Plan
@@ -589,6 +606,7 @@ def main():
                          ("mixed_errors_L511", lambda: extra_mixed_errors(torch, prec)),
                          ("fp64_L255", lambda: extra_fp64_L255(torch)),
                          ("coriolis_split_L511", lambda: extra_coriolis_split(torch, prec)),
+                         ("batched_L511_x4", lambda: extra_batched_L511(torch)),
                          ("adjoint_L255", lambda: extra_adjoint(torch)),
                          ("ensemble", lambda: extra_ensemble(torch)),
                          ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),
