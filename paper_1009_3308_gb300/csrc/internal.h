@@ -300,6 +300,23 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// Programmatic launch only for a grid that fits one wave (at most one CTA
+// per SM): a dependent launched early holds SM slots while it waits, which
+// slows a predecessor that still has CTAs to place.  The small grids of a
+// latency-bound plan gain the launch overlap; large grids launch normally.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_small(int n_sm, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t stream, Args... args) {
+    if (long(grid.x) * grid.y * grid.z <= n_sm) return launch_pdl(kernel, grid, block, smem, stream, args...);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // whole pipelines
 int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, double* out);
 int rhs_adjoint_device(sphnse_plan* P, const double* alpha, const double* w, double* out);

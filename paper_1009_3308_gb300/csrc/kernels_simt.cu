@@ -28,6 +28,10 @@ namespace sph {
 template <typename T>
 __global__ void k_prep(const double2* __restrict__ alpha, const double2* __restrict__ beta,
                        const double4_32a* __restrict__ prepc, T* __restrict__ bsyn, int N, int nf) {
+    // no early trigger: at large L this grid has several waves, and the
+    // streaming synthesis after it (programmatic launch, one CTA per SM)
+    // would hold SMs its later waves need
+    pdl_wait();   // alpha may be the predecessor's output
     const int m = blockIdx.y;
     const int K = m + blockIdx.x * blockDim.x + threadIdx.x;
     if (K > N + 1) return;
@@ -118,6 +122,8 @@ template <typename T, int NF>
 __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, const T* __restrict__ bsyn,
                                                     T* __restrict__ gsyn, const double* __restrict__ sinth,
                                                     int N, int nh, int nlat, int pairs) {
+    pdl_launch();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* B = reinterpret_cast<T*>(smem_raw);
     const int m = blockIdx.y;
@@ -183,6 +189,8 @@ __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, c
 template <typename T, int NF>
 __global__ void __launch_bounds__(128) k_analysis(const T* __restrict__ pana, const T* __restrict__ gana,
                                                    T* __restrict__ hana, int N, int nh, int nlat) {
+    pdl_launch();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // [nh][2 NF]
     const int m = blockIdx.y, par = blockIdx.z;
@@ -239,6 +247,8 @@ __global__ void k_finish(int kind, const T* __restrict__ hana, int nf, const dou
                          const double2* __restrict__ forcing, double2* __restrict__ out,
                          const int2* __restrict__ lm, const double4_32a* __restrict__ finc, int N, double nu,
                          int n, double omega_d) {
+    pdl_launch();
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int L = lm[i].x, m = lm[i].y;
@@ -351,9 +361,9 @@ static int prep_t(sphnse_plan* P, const double* alpha, const double* beta) {
     const int nf = beta ? 5 : 3;
     dim3 blk(128), grd((P->N + 2 + 127) / 128, P->N + 1);
     stage_begin(P, SPHNSE_STAGE_PREP);
-    k_prep<T><<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(alpha),
-                                           reinterpret_cast<const double2*>(beta), P->d_prepc,
-                                           reinterpret_cast<T*>(P->d_bsyn), P->N, nf);
+    launch_pdl_small(P->n_cta, k_prep<T>, grd, blk, 0, P->stream, reinterpret_cast<const double2*>(alpha),
+               reinterpret_cast<const double2*>(beta), static_cast<const double4_32a*>(P->d_prepc),
+               reinterpret_cast<T*>(P->d_bsyn), P->N, nf);
     stage_end(P, SPHNSE_STAGE_PREP);
     return check_cuda(cudaGetLastError());
 }
@@ -377,9 +387,10 @@ static int synth_t(sphnse_plan* P, int pairs) {
     if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_synthesis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    k_synthesis<T, NF><<<grd, blk, sm, P->stream>>>(
-        reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
-        reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn), P->d_s, P->N, P->nh, P->nlat, pairs);
+    launch_pdl_small(P->n_cta, k_synthesis<T, NF>, grd, blk, sm, P->stream,
+               reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
+               reinterpret_cast<const T*>(P->d_bsyn), reinterpret_cast<T*>(P->d_gsyn),
+               static_cast<const double*>(P->d_s), P->N, P->nh, P->nlat, pairs);
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(cudaGetLastError());
 }
@@ -402,9 +413,9 @@ static int anal_t(sphnse_plan* P) {
         cudaFuncSetAttribute(k_analysis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     }
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
-    k_analysis<T, NF><<<grd, blk, sm, P->stream>>>(
-        reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].ana),
-        reinterpret_cast<const T*>(P->d_gana), reinterpret_cast<T*>(P->d_hana), P->N, P->nh, P->nlat);
+    launch_pdl_small(P->n_cta, k_analysis<T, NF>, grd, blk, sm, P->stream,
+               reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].ana),
+               reinterpret_cast<const T*>(P->d_gana), reinterpret_cast<T*>(P->d_hana), P->N, P->nh, P->nlat);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
     return check_cuda(cudaGetLastError());
 }
@@ -425,7 +436,7 @@ int launch_finish(sphnse_plan* P, int kind, int prec, const double* alpha, const
     dim3 blk(256), grd((n + 255) / 256);
     stage_begin(P, SPHNSE_STAGE_FINISH);
     if (prec == SPHNSE_FP64)
-        k_finish<double><<<grd, blk, 0, P->stream>>>(kind, reinterpret_cast<const double*>(P->d_hana), nf,
+        launch_pdl_small(P->n_cta, k_finish<double>, grd, blk, 0, P->stream, kind, static_cast<const double*>(P->d_hana), nf,
                                                      reinterpret_cast<const double2*>(alpha),
                                                      reinterpret_cast<const double2*>(forcing),
                                                      reinterpret_cast<double2*>(out), P->d_lm, P->d_finc, P->N, P->nu, n,

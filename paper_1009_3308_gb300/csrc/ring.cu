@@ -188,6 +188,8 @@ struct RingArgs {
 
 template <typename T, typename TW, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_ring(RingArgs a, FFTPlan plan, const TW* __restrict__ tw) {
+    pdl_launch();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NBUF = MODE == RING_ADJOINT ? 3 : (MODE == RING_PROJECT ? 1 : 2);
     cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
@@ -289,7 +291,7 @@ static void ring_t(sphnse_plan* P, const RingArgs& a, const TW* tw, int threads,
     const int nbuf = MODE == RING_ADJOINT ? 3 : (MODE == RING_PROJECT ? 1 : 2);
     const size_t sm = size_t(nbuf) * P->nlon * sizeof(cx<T>) + size_t(P->nlon) * 2 * sizeof(T);
     cudaFuncSetAttribute(k_ring<T, TW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ring<T, TW, MODE><<<dim3(P->nlat, nb), threads, sm, P->stream>>>(a, P->fft, tw);
+    launch_pdl_small(P->n_cta, k_ring<T, TW, MODE>, dim3(P->nlat, nb), dim3(threads), sm, P->stream, a, P->fft, tw);
 }
 
 // FP32 RHS ring pass over nb instances (latitude-major buffers with strides)
@@ -771,6 +773,8 @@ int launch_ring4(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* g
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_transpose(const C* __restrict__ in, C* __restrict__ out, int R, int Cn) {
+    // no early trigger: several waves at large sizes (see k_prep)
+    pdl_wait();
     __shared__ C tile[32][33];
     const int f = blockIdx.z;
     const C* src = in + size_t(f) * R * Cn;
@@ -792,11 +796,11 @@ int launch_transpose(sphnse_plan* P, const void* in, void* out, int R, int Cn, i
     dim3 blk(32, 8), grd((Cn + 31) / 32, (R + 31) / 32, nf);
     stage_begin(P, SPHNSE_STAGE_TRANSPOSE);
     if (prec == SPHNSE_FP64)
-        k_transpose<double2><<<grd, blk, 0, P->stream>>>(reinterpret_cast<const double2*>(in),
-                                                          reinterpret_cast<double2*>(out), R, Cn);
+        launch_pdl_small(P->n_cta, k_transpose<double2>, grd, blk, 0, P->stream, reinterpret_cast<const double2*>(in),
+                   reinterpret_cast<double2*>(out), R, Cn);
     else
-        k_transpose<float2><<<grd, blk, 0, P->stream>>>(reinterpret_cast<const float2*>(in),
-                                                         reinterpret_cast<float2*>(out), R, Cn);
+        launch_pdl_small(P->n_cta, k_transpose<float2>, grd, blk, 0, P->stream, reinterpret_cast<const float2*>(in),
+                   reinterpret_cast<float2*>(out), R, Cn);
     stage_end(P, SPHNSE_STAGE_TRANSPOSE);
     return check_cuda(cudaGetLastError());
 }
