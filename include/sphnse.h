@@ -294,10 +294,12 @@ typedef struct sphnse_ensemble sphnse_ensemble;
  * The ensemble owns its state vectors (see sphnse_ensemble_instance).
  * Returns NULL on error. */
 sphnse_ensemble* sphnse_ensemble_create(int n, const int* L, const double* nu, double Omega);
+/* (FP32 contractions by default; SPHNSE_KEY_PRECISION selects BF16X3.) */
 void sphnse_ensemble_destroy(sphnse_ensemble* ens);
 
-/* SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX (and
- * _PRECISION, FP32 only). */
+/* SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX and
+ * _PRECISION (SPHNSE_FP32, default, or SPHNSE_BF16X3: instances of one
+ * truncation then share every table tile on the tensor cores). */
 int sphnse_ensemble_set(sphnse_ensemble* ens, int key, double value);
 /* Read SPHNSE_KEY_RTOL, _ATOL, _MAX_ORDER, _NEWTON_MAX_ITER, _H_MAX,
  * _PRECISION or _ROUNDS into *value. */
