@@ -239,6 +239,14 @@ class Integrator:
             self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), ctypes.byref(info)))
         return info.as_dict()
 
+    def advance(self, nsteps):
+        """nsteps accepted steps in one library call; their infos."""
+        infos = (StepInfo * int(nsteps))()
+        self.plan._stream()
+        check("sphnse_advance", _capi.lib().sphnse_advance(
+            self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), int(nsteps), ctypes.cast(infos, ctypes.c_void_p)))
+        return [x.as_dict() for x in infos]
+
     def replay_step(self, h, k, newton_max=50):
         info = StepInfo()
         self.plan._stream()

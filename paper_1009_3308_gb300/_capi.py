@@ -54,6 +54,8 @@ _SIGS = {
     "sphnse_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sphnse_state_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "sphnse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.POINTER(StepInfo)]),
+    "sphnse_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_void_p]),
     "sphnse_replay_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(StepInfo)]),
     "sphnse_rhs_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p]),

@@ -109,6 +109,16 @@ struct TcBatchA {
 };
 
 // tcgen05 path state (tensor maps and item schedules, built on first use)
+// Device-side simplified-Newton loop of one corrector (a CUDA graph with a
+// conditional WHILE node): inputs written by the host per attempt, state and
+// results updated by the loop's control kernel.
+struct NewtonCtl {
+    double c, nu, omega, thr, rtol, rate;   // inputs (rate: the running contraction estimate)
+    int k, maxit, tight, fp64, havrate, pad0;
+    double nrm[4], ynorm, oldnrm;           // results / loop state
+    int it, its, conv, stop, nonfinite, pad1;
+};
+
 // staging of sphnse_rhs_host: two slots, an upload and a download stream
 struct HostIO {
     void* din[2] = {nullptr, nullptr};
@@ -210,6 +220,14 @@ struct sphnse_plan {
     bool stage_rec[8] = {};      // the current launch of the stage is recorded
     std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];
     sph::HostIO hio;
+    // device-side Newton loop (sphnse_step, sphnse_replay_step)
+    cudaGraphExec_t ng_exec = nullptr;
+    const void* ng_key[4] = {nullptr, nullptr, nullptr, nullptr};   // alpha, dif, forcing, precision + split
+    double ng_nu = 0, ng_omega = 0;
+    bool ng_failed = false;              // capture not possible here: the host loop runs
+    sph::NewtonCtl* d_ctl = nullptr;
+    sph::NewtonCtl* h_ctl = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for capturing the loop body
     int ev_used[SPHNSE_NSTAGES] = {0};
     double stage_ms[SPHNSE_NSTAGES] = {0};
     long stage_n[SPHNSE_NSTAGES] = {0};

@@ -171,6 +171,84 @@ __global__ void k_newton(const double2* F, const double2* y, const double2* y0, 
     block_amax_f<4>(slot, nv, id, bad);
 }
 
+// The same update with its parameters read from the device-side loop state
+// (a graph node keeps fixed arguments; c, k and the weights change per attempt)
+__global__ void k_newton_g(const double2* F, const double2* y, const double2* y0, const double2* psi, double2* d,
+                           double2* ynew, const double2* dif, const int2* lm, const NewtonCtl* ctl,
+                           unsigned long long* slot, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = ctl->k;
+    float nv[4] = {0.f, 0.f, 0.f, 0.f};
+    bool bad = false;
+    if (i < n) {
+        const int2 q = lm[i];
+        const NewtonEntry e = newton_entry(q.x, q.y, ctl->c, float(ctl->nu), float(2.0 * ctl->omega),
+                                           fmaxf(float(ctl->thr), 1e-30f), F[i], psi[i], d[i], y[i], ynew[i], y0[i],
+                                           k >= 2 ? dif + size_t(k - 1) * n + i : nullptr, dif[size_t(k) * n + i]);
+        d[i] = e.dn;
+        ynew[i] = e.yv;
+        for (int j = 0; j < 4; ++j) nv[j] = e.nv[j];
+        bad = e.bad;
+    }
+    const int id[4] = {0, 1, 2, 3};
+    block_amax_f<4>(slot, nv, id, bad);
+}
+
+// One thread: the corrector's stopping rule after iteration ctl->it (the same
+// tests as the host loop), then clear the slots the next iteration fills and
+// set the WHILE condition (0: stop).
+__global__ void k_newton_ctl(NewtonCtl* ctl, unsigned long long* slots, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double eps = 2.220446049250313e-16;
+    const int it = ctl->it;
+    bool stop = false, conv = false;
+    if (slots[7]) {
+        ctl->nonfinite = 1;
+        stop = true;
+    } else {
+        double nv[4];
+        for (int q = 0; q < 4; ++q) nv[q] = __longlong_as_double(static_cast<long long>(slots[q]));
+        if (it == 0) ctl->ynorm = __longlong_as_double(static_cast<long long>(slots[4]));
+        ctl->its = it + 1;
+        for (int q = 0; q < 4; ++q) ctl->nrm[q] = nv[q];
+        const double newnrm = nv[0], minnrm = 100.0 * eps * ctl->ynorm, oldnrm = ctl->oldnrm;
+        const double rtol = ctl->rtol;
+        if (ctl->tight) {
+            const bool stalled = !ctl->fp64 && it >= 3 && newnrm > 0.8 * oldnrm;
+            if (newnrm <= fmax(minnrm, 1e-15) || stalled) stop = conv = true;
+        } else if (newnrm <= minnrm) {
+            stop = conv = true;
+        } else if (it == 0) {
+            if (ctl->havrate) {
+                const double errit = newnrm * ctl->rate / (1.0 - ctl->rate);
+                if (errit <= 0.05 * rtol) stop = conv = true;
+            } else {
+                ctl->rate = 0.0;
+            }
+        } else if (newnrm > 0.9 * oldnrm) {
+            stop = true;   // too slow
+        } else {
+            ctl->rate = fmax(0.9 * ctl->rate, newnrm / oldnrm);
+            ctl->havrate = 1;
+            const double errit = newnrm * ctl->rate / (1.0 - ctl->rate);
+            if (errit <= 0.5 * rtol) stop = conv = true;
+            else if (it == ctl->maxit - 1) stop = true;
+            else if (0.5 * rtol < errit * pow(ctl->rate, double(ctl->maxit - 1 - it))) stop = true;
+        }
+        ctl->oldnrm = newnrm;
+        if (!stop && it + 1 >= ctl->maxit) {
+            stop = true;
+            conv = ctl->tight != 0;   // the host loop: a tight loop that ran out counts as converged
+        }
+    }
+    ctl->it = it + 1;
+    ctl->conv = conv;
+    ctl->stop = stop;
+    for (int q = 0; q < 4; ++q) slots[q] = 0ull;
+    slots[7] = 0ull;
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
 // D_{k+1} = d - D_k; D_k = d; D_j += D_{j+1} (j = k-1..0); y = ynew
 __global__ void k_accept(double2* dif, const double2* d, double2* y, const double2* ynew, int k, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -438,6 +516,80 @@ int rescale(sphnse_plan* P, sphnse_state* st, double h, int k) {
     return stage_launch_check(P);
 }
 
+// The corrector's Newton loop as one graph launch: a WHILE node whose body is
+// the RHS at ynew, the Newton update and the control kernel, which sets the
+// loop condition on the device, so an attempt costs one host round trip
+// instead of one per iteration.  Built per (state, forcing, precision, nu,
+// Omega) after the plan's kernels are set up; any failure to capture leaves
+// the host loop in charge.
+bool newton_graph_ready(sphnse_plan* P, sphnse_state* st, const double* forcing) {
+    if (P->ng_failed || P->timing) return false;
+    const void* key[4] = {st->alpha, st->dif, forcing,
+                          reinterpret_cast<const void*>(uintptr_t(P->precision) | (uintptr_t(P->coriolis_split) << 8))};
+    if (P->ng_exec && std::equal(key, key + 4, P->ng_key) && P->ng_nu == P->nu && P->ng_omega == P->Omega) return true;
+    if (P->ng_exec) {
+        cudaGraphExecDestroy(P->ng_exec);
+        P->ng_exec = nullptr;
+    }
+    if (!P->d_ctl && (cudaMalloc(reinterpret_cast<void**>(&P->d_ctl), sizeof(NewtonCtl)) != cudaSuccess ||
+                      cudaMallocHost(reinterpret_cast<void**>(&P->h_ctl), sizeof(NewtonCtl)) != cudaSuccess)) {
+        P->ng_failed = true;
+        return false;
+    }
+    if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        P->ng_failed = true;
+        return false;
+    }
+    // the body's kernels must not set anything up while being captured
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return false;
+    Work W = work(P);
+    const int n = P->n_coeff;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const cudaStream_t saved = P->stream;
+        P->stream = P->cap_stream;
+        ok = cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+             cudaSuccess;
+        if (ok) {
+            const int rc = rhs_device(P, reinterpret_cast<const double*>(W.ynew), forcing,
+                                      reinterpret_cast<double*>(W.F));
+            k_newton_g<<<grid(n), 256, 0, P->cap_stream>>>(
+                W.F, reinterpret_cast<const double2*>(st->alpha), W.y0, W.psi, W.d, W.ynew,
+                reinterpret_cast<const double2*>(st->dif), P->d_lm, P->d_ctl, P->d_norms, n);
+            k_newton_ctl<<<1, 32, 0, P->cap_stream>>>(P->d_ctl, P->d_norms, h);
+            cudaGraph_t out = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &out);
+            ok = rc == SPHNSE_OK && ce == cudaSuccess;
+        }
+        P->stream = saved;
+    }
+    if (ok) ok = cudaGraphInstantiate(&P->ng_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves no sticky error; clear the last one
+    if (!ok) {
+        P->ng_exec = nullptr;
+        P->ng_failed = true;
+        return false;
+    }
+    std::copy(key, key + 4, P->ng_key);
+    P->ng_nu = P->nu;
+    P->ng_omega = P->Omega;
+    return true;
+}
+
 // Predictor + simplified Newton.  tight: iterate until the update norm is
 // below max(minnrm, 1e-15) (replay).  Returns SPHNSE_OK / error; *conv set.
 int corrector(sphnse_plan* P, sphnse_state* st, const double* forcing, double h, int k, bool tight, int maxit,
@@ -461,6 +613,33 @@ int corrector(sphnse_plan* P, sphnse_state* st, const double* forcing, double h,
     stage_end(P, SPHNSE_STAGE_STEP);
     if ((rc = stage_launch_check(P))) return rc;
     const double cc = h * C.iga[k - 1];
+    if (newton_graph_ready(P, st, forcing)) {
+        NewtonCtl& q = *P->h_ctl;
+        std::memset(&q, 0, sizeof(q));
+        q.c = cc;
+        q.nu = P->nu;
+        q.omega = P->Omega;
+        q.thr = thr;
+        q.rtol = P->rtol;
+        q.rate = st->rate;
+        q.havrate = st->havrate;
+        q.k = k;
+        q.maxit = maxit;
+        q.tight = tight;
+        q.fp64 = P->precision == SPHNSE_FP64;
+        if (cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(NewtonCtl), cudaMemcpyHostToDevice, P->stream) != cudaSuccess ||
+            cudaGraphLaunch(P->ng_exec, P->stream) != cudaSuccess ||
+            cudaMemcpyAsync(P->h_ctl, P->d_ctl, sizeof(NewtonCtl), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+            cudaStreamSynchronize(P->stream) != cudaSuccess)
+            return SPHNSE_E_CUDA;
+        if (q.nonfinite) return SPHNSE_E_NONFINITE;
+        *conv = q.conv != 0;
+        *its = q.its;
+        for (int j = 0; j < 4; ++j) norms[j] = q.nrm[j];
+        st->rate = q.rate;
+        st->havrate = q.havrate;
+        return SPHNSE_OK;
+    }
     const double eps = 2.220446049250313e-16;
     double oldnrm = 0.0, ynorm = 0.0;
     *conv = false;
@@ -675,6 +854,15 @@ int sphnse_step(sphnse_plan* P, sphnse_state* st, const double* forcing, sphnse_
         return SPHNSE_OK;
     }
     return SPHNSE_E_STEP_TOO_SMALL;
+}
+
+int sphnse_advance(sphnse_plan* P, sphnse_state* st, const double* forcing, int nsteps, sphnse_step_info* info) {
+    if (!P || !st || nsteps < 0) return SPHNSE_E_ARG;
+    for (int s = 0; s < nsteps; ++s) {
+        const int rc = sphnse_step(P, st, forcing, info ? info + s : nullptr);
+        if (rc) return rc;
+    }
+    return SPHNSE_OK;
 }
 
 int sphnse_replay_step(sphnse_plan* P, sphnse_state* st, const double* forcing, double h, int k, int newton_max,

@@ -183,6 +183,10 @@ static void destroy_plan(sphnse_plan* P) {
     for (auto& t : P->tab) free_tables(t);
     tc_free(P);
     host_io_free(P);
+    if (P->ng_exec) cudaGraphExecDestroy(P->ng_exec);
+    if (P->d_ctl) cudaFree(P->d_ctl);
+    if (P->h_ctl) cudaFreeHost(P->h_ctl);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
                     P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_ftw, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
                     P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};

@@ -125,3 +125,19 @@ def test_step_argument_errors():
         integ.replay_step(1e-3, 7)
     with pytest.raises(SphnseError, match="E_ARG"):
         integ.replay_step(-1.0, 1)
+
+
+def test_advance_equals_repeated_steps():
+    """sphnse_advance(n) takes exactly the steps of n sphnse_step calls."""
+    from paper_1009_3308_gb300 import Integrator
+    w, c, prob, plan = _l31()
+    a0, f = w["alpha0"], w["forcing"]
+    plan.set("RTOL", c["rtol"])
+    plan.set("ATOL", 1e-3 * c["rtol"] * float(np.max(np.abs(a0))))
+    i1 = Integrator(plan, _dev(a0), forcing=_dev(f))
+    ref = [i1.step() for _ in range(15)]
+    i2 = Integrator(plan, _dev(a0), forcing=_dev(f))
+    got = i2.advance(15)
+    assert [g["h"] for g in got] == [r["h"] for r in ref]
+    assert [g["order"] for g in got] == [r["order"] for r in ref]
+    assert torch.equal(i1.alpha, i2.alpha)
