@@ -315,6 +315,70 @@ def extra_batched_L511(torch, n=4, reps=200):
     return {"states": n, "rhs_per_s": n * reps / el, "us_per_batched_rhs": 1e6 * el / reps}
 
 
+def run_example2(torch, t_out=(10, 20, 30, 40, 50, 60), N=100, N1=75, rtol=1e-3, precision="fp64"):
+    """Sec. 5 Example 2 (N = 100, Omega = 1, nu = 1e-4, rtol 1e-3): the random
+    initial state of degree <= 20 driven by fhat_{3,0}(t), integrated to
+    t = 60; at each output time the spectrum E(L) of U_75 = P_75 u_N and of
+    the approximate inertial manifold Phi_150(U_75) (Eq. (eq:p-p)).  The
+    forcing of a step is fhat_{3,0} at the end of the step the controller
+    plans (the step API holds it constant over a step)."""
+    import numpy as np
+    from paper_1009_3308_gb300 import Integrator, Plan
+    from seeded_inputs import example2, example2_forcing_30
+    nu = 1e-4
+    plan = Plan(N, 162, 324, nu, 1.0, precision=precision)
+    plan.set("RTOL", rtol)
+    a0 = example2(N)
+    plan.set("ATOL", 1e-3 * rtol * float(np.abs(a0).max()))
+    p2 = Plan(2 * N1, 243, 486, nu, 1.0)
+    f = torch.zeros(plan.n_coeff, dtype=torch.complex128, device="cuda")
+    f2 = torch.zeros(p2.n_coeff, dtype=torch.complex128, device="cuda")
+    f[2] = example2_forcing_30(0.0)       # packed index of (L = 3, m = 0)
+    it = Integrator(plan, torch.from_numpy(a0).cuda(), forcing=f, t_end=t_out[0])
+    out, steps, rhs = [], 0, 0
+
+    def spectra(t):
+        a = it.alpha
+        E = plan.energy_spectrum(a).cpu().numpy()[: N1 + 1]
+        f2[2] = example2_forcing_30(t)
+        phi = p2.inertial_manifold(N1, p2.resize(a, N, L_max=N1), f2)
+        Ep = p2.energy_spectrum(phi).cpu().numpy()
+        return E, Ep
+
+    E0, _ = spectra(0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for te in t_out:
+        it.st.t_end = float(te)
+        while it.t < te * (1 - 1e-12):
+            f[2] = example2_forcing_30(min(te, it.t + it.st.h))
+            info = it.step()
+            steps += 1
+            rhs += info["rhs_evals"]
+        E, Ep = spectra(te)
+        out.append((te, E, Ep))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return E0, out, steps, rhs, el
+
+
+def extra_example2(torch):
+    import numpy as np
+    E0, out, steps, rhs, el = run_example2(torch)
+    L = np.arange(len(E0))
+    cen = lambda E: float((L[1:] * E[1:]).sum() / E[1:].sum())
+    rows = []
+    for te, E, Ep in out:
+        Lp = np.arange(76, len(Ep))
+        y = np.log(np.maximum(Lp ** 4 * Ep[76:], 1e-300))
+        slope = float(np.polyfit(Lp, y, 1)[0])
+        rows.append({"t": te, "energy_U75": float(E.sum()), "centroid_L": cen(E),
+                     "L4E_phi_slope_per_L": slope, "E_phi_total": float(Ep.sum())})
+    return {"steps": steps, "rhs_evals": rhs, "seconds": el, "steps_per_s": steps / el,
+            "energy_t0": float(E0.sum()), "centroid_L_t0": cen(E0), "outputs": rows,
+            "precision": "fp64", "N": 100, "N1": 75, "rtol": 1e-3}
+
+
 def extra_L31(torch, nsteps=100):
     """The L = 31 workload: 100 adaptive FP64 steps, rtol 1e-8, steady forcing."""
     from paper_1009_3308_gb300 import Integrator, Plan
@@ -610,7 +674,8 @@ def main():
                          ("adjoint_L255", lambda: extra_adjoint(torch)),
                          ("ensemble", lambda: extra_ensemble(torch)),
                          ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),
-                         ("L31_fp64_steps", lambda: extra_L31(torch))):
+                         ("L31_fp64_steps", lambda: extra_L31(torch)),
+                         ("example2_N100", lambda: extra_example2(torch))):
             try:
                 extras[name] = fn()
             except Exception as e:  # an extra must not hide the headline line

@@ -87,6 +87,26 @@ def workload(name):
     return out
 
 
+def example2(N=100, seed=2020, nu=1e-4, Lmax=20):
+    """Initial state of Sec. 5 Example 2: alpha_{L,m} = a_L exp(i phi_{L,m})
+    for L <= Lmax and m >= 0 (phi_{L,0} = 0; reading: an independent phase
+    per (L, m)), zero above Lmax; a_L = b_L / ||b||, b_L = 2 / (L + (nu L)^2.5).
+    Negative orders follow from the packed symmetry."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    Ls, ms = packed_orders(N)
+    b = np.array([2.0 / (L + (nu * L) ** 2.5) for L in range(1, Lmax + 1)])
+    a = b / np.linalg.norm(b)
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=Ls.size)
+    phi[ms == 0] = 0.0
+    amp = np.where(Ls <= Lmax, a[np.minimum(Ls, Lmax) - 1], 0.0)
+    return (amp * np.exp(1j * phi)).astype(np.complex128)
+
+
+def example2_forcing_30(t):
+    """The only nonzero forcing coefficient of Example 2, fhat_{3,0}(t)."""
+    return 1.0 if t <= 10.0 else math.cos(math.pi * t / 5.0) * math.exp(-(t - 10.0) / 5.0)
+
+
 def ensemble(n_instances=256, degrees=(63, 127, 255), seed0=1000, decay=0.05,
              nu_range=(1e-5, 1e-3)):
     """Batched-ensemble members: per instance a truncation drawn uniformly
