@@ -171,14 +171,21 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, x):
+def max_over_ranks(world, x, device="cuda"):
+    """The slowest rank's value of x (a duration), on every rank."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` independent replicas that each
+    processed `units_per_rank` units, timed by the slowest rank."""
+    return world * units_per_rank / seconds
 
 
 def time_rhs(plan, a, out, steps, torch):
@@ -604,7 +611,7 @@ def main():
     stage = {name: {"ms": st_ms[i], "launches": st_n[i]} for i, name in enumerate(_capi.STAGES)}
     launches = kernels_per_rhs * args.steps
 
-    value = world * args.steps / (ms_total / 1e3)
+    value = replica_rate(world, args.steps, ms_total / 1e3)
     ms_per_step = ms_total / args.steps
 
     # dominant kernel and its roofline (live durations from the timed region)
@@ -644,7 +651,7 @@ def main():
     chk += float(pin_out[(k_e2e - 1) & 1][1].real)
     el = time.perf_counter() - t0
     el = max_over_ranks(world, el)
-    e2e = {"value": world * k_e2e / el, "unit": UNIT, "h2d_bytes_per_step": pin_in[0].numel() * 16,
+    e2e = {"value": replica_rate(world, k_e2e, el), "unit": UNIT, "h2d_bytes_per_step": pin_in[0].numel() * 16,
            "d2h_bytes_per_step": pin_out[0].numel() * 16, "steps": k_e2e,
            "api": "sphnse_rhs_host (pinned host buffers, copies overlapped with the previous step's RHS)",
            "finite": bool(np.isfinite(chk))}
