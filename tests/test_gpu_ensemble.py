@@ -99,3 +99,32 @@ def test_ensemble_advance_equals_independent_integrators(precision):
         ref = it.alpha.cpu().numpy()
         got = ens.get(i).cpu().numpy()
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref), i
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 3e-5), ("bf16x3", 3e-5)])
+def test_full_ensemble_rhs_matches_oracle_on_sampled_members(precision, tol):
+    """The 256-member ensemble (L uniform over {63, 127, 255}, nu log-uniform
+    in [1e-5, 1e-3]) in one batched RHS, as the ensemble benchmark runs it:
+    two members of every truncation against the FP64 oracle's Galerkin RHS
+    (Eq. (ode)); the rest must be finite."""
+    from oracle.rhs import Problem, rhs_separable
+    from paper_1009_3308_gb300 import Ensemble
+    from seeded_inputs import ensemble
+    mem = ensemble(256)
+    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0, precision=precision)
+    for i, m in enumerate(mem):
+        ens.set_alpha(i, _dev(m["alpha0"]))
+    ens.rhs()
+    torch.cuda.synchronize()
+    picked = []
+    for L in (63, 127, 255):
+        idx = [i for i, m in enumerate(mem) if m["L"] == L]
+        picked += [idx[0], idx[-1]]
+    for i in picked:
+        m = mem[i]
+        ref = rhs_separable(Problem(m["L"], m["nlon"], m["nu"], m["Omega"]), m["alpha0"])
+        got = ens.get(i, "F").cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= tol, (i, m["L"], err)
+    for i in range(len(mem)):
+        assert torch.isfinite(torch.view_as_real(ens.get(i, "F"))).all(), i
