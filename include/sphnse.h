@@ -237,15 +237,17 @@ int sphnse_state_init(sphnse_plan* plan, sphnse_state* st, double t0, double h0,
  * iteration matrix I - c J_d, J_d = -nu lambda + 2 i Omega m / lambda,
  * local error estimate, step rejection and order/step selection (the
  * MATLAB ODE-suite scheme the paper follows).  forcing: (device) steady over
- * the step, or NULL.  Fills *info (host).  The Newton iterations of an
- * attempt run as one CUDA-graph launch whose loop condition is set on the
- * device (one host synchronisation per attempt; with stage timing enabled
- * the iterations are launched one by one from the host instead). */
+ * the step, or NULL.  Fills *info (host).  The attempts, their Newton
+ * iterations and the controller run as one CUDA-graph launch whose loop
+ * conditions are set on the device (one host synchronisation per call);
+ * with stage timing enabled the host drives the attempts instead. */
 int sphnse_step(sphnse_plan* plan, sphnse_state* st, const double* forcing,
                 sphnse_step_info* info);
 
-/* nsteps >= 0 accepted steps of sphnse_step in one call (no return to the
- * caller between steps); info: host array of nsteps entries or NULL. */
+/* nsteps >= 0 accepted steps of sphnse_step in one call and one graph
+ * launch (no host synchronisation between steps); info: host array of
+ * nsteps entries or NULL.  On an error the state holds the steps accepted
+ * before it, and info their entries. */
 int sphnse_advance(sphnse_plan* plan, sphnse_state* st, const double* forcing, int nsteps,
                    sphnse_step_info* info);
 

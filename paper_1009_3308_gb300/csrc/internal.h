@@ -119,6 +119,29 @@ struct NewtonCtl {
     int it, its, conv, stop, nonfinite, pad1;
 };
 
+// State of the device-side step loop (sphnse_advance as one graph launch):
+// the controller's inputs and memory, loaded from the sphnse_state before the
+// launch and stored back after it, and the current attempt's parameters that
+// the loop's kernels read.
+struct StepCtl {
+    double rtol, thr, h_max;                 // per call
+    int maxk, newton_max, fp64, nsteps;
+    double nu, omega;
+    double gamma[SPHNSE_MAXK], iga[SPHNSE_MAXK], ec[SPHNSE_MAXK];
+    sphnse_step_info* info;                  // nsteps entries (device in the graph, host otherwise) or null
+    double t, h, t_end, h_dif, rate, miter_h;  // integrator state (sphnse_state)
+    int order, nconhk, havrate, miter_k;
+    int done, attempt, nofailed, rejections, newton_total, rhs_evals;
+    double h_dif_before;
+    int status;                              // SPHNSE_OK, else the error that ended the loop
+    int k, do_rescale;                       // the current attempt
+    int accept, k_acc;                       // the last attempt was accepted at order k_acc
+    double h_att;
+    double A[SPHNSE_MAXK * SPHNSE_MAXK];     // difference rescaling matrix (do_rescale)
+    double g[SPHNSE_MAXK];                   // predictor weights of psi
+    NewtonCtl nc;
+};
+
 // staging of sphnse_rhs_host: two slots, an upload and a download stream
 struct HostIO {
     void* din[2] = {nullptr, nullptr};
@@ -228,6 +251,17 @@ struct sphnse_plan {
     sph::NewtonCtl* d_ctl = nullptr;
     sph::NewtonCtl* h_ctl = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for capturing the loop body
+    // device-side step loop (sphnse_advance, sphnse_step): outer WHILE over
+    // attempts, the Newton WHILE nested in its body
+    cudaGraphExec_t sg_exec = nullptr;
+    const void* sg_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    double sg_nu = 0, sg_omega = 0;
+    bool sg_failed = false;
+    sph::StepCtl* d_step = nullptr;
+    sph::StepCtl* h_step = nullptr;      // pinned
+    sphnse_step_info* d_info = nullptr;
+    sphnse_step_info* h_info = nullptr;  // pinned
+    int info_cap = 0;
     int ev_used[SPHNSE_NSTAGES] = {0};
     double stage_ms[SPHNSE_NSTAGES] = {0};
     long stage_n[SPHNSE_NSTAGES] = {0};

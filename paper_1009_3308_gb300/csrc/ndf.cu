@@ -1,7 +1,7 @@
 // Variable-order, variable-step NDF integrator (Sec. 4.2, Eq. (ode_disc)),
 // its frozen-controller replay, and the discrete adjoint of that replay.
 //
-// The controller (host) follows the quasi-constant step-size NDF scheme of
+// The controller follows the quasi-constant step-size NDF scheme of
 // the MATLAB ODE suite that the paper cites: backward differences D_j =
 // nabla^{j+1} alpha_n, predictor alpha0 = alpha_n + sum_{j<k} D_j, corrector
 //   c F(t_{n+1}, alpha0 + d) - psi - d = 0,  c = h / ((1 - kappa_k) gamma_k),
@@ -12,8 +12,10 @@
 // (kappa_k gamma_k + 1/(k+1)) ||d / wt||_inf, wt = max(|alpha_n|,
 // |alpha_{n+1}|, atol/rtol) per real component; order and step selection from
 // the estimates of orders k-1, k, k+1; difference rescaling by R(rho) U on a
-// step-size change.  All vector work is FP64 on the device; the host reads
-// four norms per Newton iteration.
+// step-size change.  All vector work is FP64 on the device.  The controller
+// (att_begin / att_end, newton_control) runs on the device inside one graph
+// launch per call (nested WHILE nodes over attempts and Newton iterations),
+// or on the host with the same functions when stage timing is on.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,8 +51,9 @@ struct NDFConst {
 struct Mat { double a[SPHNSE_MAXK * SPHNSE_MAXK]; };
 struct Coef { double c[SPHNSE_MAXK]; };
 
-// (R(rho) U)[:k, :k], R_ij = prod_{l=1..i} (l - 1 - j rho) / l, U = R(1)
-Mat rescale_matrix(int k, double rho) {
+// (R(rho) U)[:k, :k], R_ij = prod_{l=1..i} (l - 1 - j rho) / l, U = R(1),
+// into A (row-major SPHNSE_MAXK x SPHNSE_MAXK, zero outside k x k)
+__host__ __device__ inline void rescale_matrix_into(int k, double rho, double* A) {
     double R[SPHNSE_MAXK][SPHNSE_MAXK], U[SPHNSE_MAXK][SPHNSE_MAXK];
     for (int j = 1; j <= k; ++j) {
         double r = 1.0, u = 1.0;
@@ -61,15 +64,221 @@ Mat rescale_matrix(int k, double rho) {
             U[i - 1][j - 1] = u;
         }
     }
-    Mat m;
-    std::memset(&m, 0, sizeof(m));
+    for (int i = 0; i < SPHNSE_MAXK * SPHNSE_MAXK; ++i) A[i] = 0.0;
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) {
             double s = 0.0;
             for (int l = 0; l < k; ++l) s += R[i][l] * U[l][j];
-            m.a[i * SPHNSE_MAXK + j] = s;
+            A[i * SPHNSE_MAXK + j] = s;
         }
+}
+
+Mat rescale_matrix(int k, double rho) {
+    Mat m;
+    rescale_matrix_into(k, rho, m.a);
     return m;
+}
+
+// Corrector parameters of one attempt (tight: iterate to the rounding level,
+// for the replay).
+__host__ __device__ inline void newton_init(NewtonCtl& q, double c, double nu, double omega, double thr, double rtol,
+                                            double rate, int havrate, int k, int maxit, int tight, int fp64) {
+    q = NewtonCtl{};
+    q.c = c;
+    q.nu = nu;
+    q.omega = omega;
+    q.thr = thr;
+    q.rtol = rtol;
+    q.rate = rate;
+    q.havrate = havrate;
+    q.k = k;
+    q.maxit = maxit;
+    q.tight = tight;
+    q.fp64 = fp64;
+}
+
+// The corrector's stopping rule after iteration q.it, from the norms of that
+// iteration (nv[0..3]: the slots of the Newton update, nv[4]: the predictor's
+// scale, read at the first iteration).  Convergence and rate tests of the
+// MATLAB ODE suite's simplified Newton; returns true when the loop stops.
+__host__ __device__ inline bool newton_control(NewtonCtl& q, const double* nv, bool nonfinite) {
+    const double eps = 2.220446049250313e-16;
+    const int it = q.it;
+    bool stop = false, conv = false;
+    if (nonfinite) {
+        q.nonfinite = 1;
+        stop = true;
+    } else {
+        if (it == 0) q.ynorm = nv[4];
+        q.its = it + 1;
+        for (int j = 0; j < 4; ++j) q.nrm[j] = nv[j];
+        const double newnrm = nv[0], minnrm = 100.0 * eps * q.ynorm, oldnrm = q.oldnrm;
+        const double rtol = q.rtol;
+        if (q.tight) {
+            // converged to the rounding level: below 1e-15 in the weighted
+            // norm, or no longer shrinking (FP32 / BF16 contractions stall at
+            // their own rounding level long before 1e-15)
+            const bool stalled = !q.fp64 && it >= 3 && newnrm > 0.8 * oldnrm;
+            if (newnrm <= fmax(minnrm, 1e-15) || stalled) stop = conv = true;
+        } else if (newnrm <= minnrm) {
+            stop = conv = true;
+        } else if (it == 0) {
+            if (q.havrate) {
+                const double errit = newnrm * q.rate / (1.0 - q.rate);
+                if (errit <= 0.05 * rtol) stop = conv = true;
+            } else {
+                q.rate = 0.0;
+            }
+        } else if (newnrm > 0.9 * oldnrm) {
+            stop = true;   // too slow
+        } else {
+            q.rate = fmax(0.9 * q.rate, newnrm / oldnrm);
+            q.havrate = 1;
+            const double errit = newnrm * q.rate / (1.0 - q.rate);
+            if (errit <= 0.5 * rtol) stop = conv = true;
+            else if (it == q.maxit - 1) stop = true;
+            else if (0.5 * rtol < errit * pow(q.rate, double(q.maxit - 1 - it))) stop = true;
+        }
+        q.oldnrm = newnrm;
+        if (!stop && it + 1 >= q.maxit) {
+            stop = true;
+            conv = q.tight != 0;   // a tight loop that ran out counts as converged
+        }
+    }
+    q.it = it + 1;
+    q.conv = conv;
+    q.stop = stop;
+    return stop;
+}
+
+constexpr double EPS16 = 16.0 * 2.220446049250313e-16;
+
+// Start an attempt: clamp h to [16 eps |t|, h_max] and to t_end, rescale the
+// differences to it if it changed, reset the rate memory on a new (h, k) and
+// set the predictor weights and the corrector's parameters.
+__host__ __device__ inline void att_begin(StepCtl& S) {
+    if (S.attempt == 0) {
+        S.h_dif_before = S.h_dif;
+        S.nofailed = 1;
+        S.rejections = 0;
+        S.newton_total = 0;
+        S.rhs_evals = 0;
+    }
+    const double hmin = EPS16 * fabs(S.t);
+    double h = fmin(S.h_max, fmax(hmin, S.h));
+    if (1.1 * h >= S.t_end - S.t) h = S.t_end - S.t;
+    S.h = h;
+    S.h_att = h;
+    const int k = S.order;
+    S.k = k;
+    S.do_rescale = h != S.h_dif;
+    if (S.do_rescale) {
+        rescale_matrix_into(k, h / S.h_dif, S.A);
+        S.h_dif = h;
+        S.nconhk = 0;
+    }
+    if (h != S.miter_h || k != S.miter_k) {
+        S.havrate = 0;
+        S.miter_h = h;
+        S.miter_k = k;
+    }
+    for (int j = 0; j < SPHNSE_MAXK; ++j) S.g[j] = j < k ? S.gamma[j] * S.iga[k - 1] : 0.0;
+    newton_init(S.nc, h * S.iga[k - 1], S.nu, S.omega, S.thr, S.rtol, S.rate, S.havrate, k, S.newton_max, 0, S.fp64);
+}
+
+// Finish an attempt from the corrector's results: reject (a smaller h, maybe
+// a lower order) or accept (advance t, record the step, choose the next
+// order and step size from the error estimates of orders k - 1, k, k + 1).
+__host__ __device__ inline void att_end(StepCtl& S) {
+    const NewtonCtl& q = S.nc;
+    S.rate = q.rate;
+    S.havrate = q.havrate;
+    S.accept = 0;
+    if (q.nonfinite) {
+        S.status = SPHNSE_E_NONFINITE;
+        return;
+    }
+    const int k = S.k;
+    const double h = S.h_att, hmin = EPS16 * fabs(S.t);
+    S.newton_total += q.its;
+    S.rhs_evals += q.its;
+    const double err = q.nrm[1] * S.ec[k - 1];
+    if (!q.conv || err > S.rtol) {
+        ++S.rejections;
+        if (h <= hmin) {
+            S.status = SPHNSE_E_STEP_TOO_SMALL;
+            return;
+        }
+        if (!q.conv) {
+            S.h = fmax(hmin, 0.3 * h);
+        } else if (S.nofailed) {
+            S.nofailed = 0;
+            double hopt = h * fmax(0.1, 0.833 * pow(S.rtol / err, 1.0 / (k + 1)));
+            if (k > 1) {
+                const double errkm1 = q.nrm[2] * S.ec[k - 2];
+                const double hkm1 = h * fmax(0.1, 0.769 * pow(S.rtol / errkm1, 1.0 / k));
+                if (hkm1 > hopt) {
+                    hopt = fmin(h, hkm1);
+                    S.order = k - 1;
+                }
+            }
+            S.h = fmax(hmin, hopt);
+        } else {
+            S.h = fmax(hmin, 0.5 * h);
+        }
+        if (++S.attempt >= 200) S.status = SPHNSE_E_STEP_TOO_SMALL;
+        return;
+    }
+    // accepted
+    S.accept = 1;
+    S.k_acc = k;
+    S.t += h;
+    S.nconhk = S.nconhk + 1 < SPHNSE_MAXK + 2 ? S.nconhk + 1 : SPHNSE_MAXK + 2;
+    if (S.nconhk >= k + 2) {
+        double temp = 1.2 * pow(err / S.rtol, 1.0 / (k + 1));
+        double hopt = temp > 0.1 ? h / temp : 10.0 * h;
+        int kopt = k;
+        if (k > 1) {
+            const double errkm1 = q.nrm[2] * S.ec[k - 2];
+            temp = 1.3 * pow(errkm1 / S.rtol, 1.0 / k);
+            const double hkm1 = temp > 0.1 ? h / temp : 10.0 * h;
+            if (hkm1 > hopt) {
+                hopt = hkm1;
+                kopt = k - 1;
+            }
+        }
+        if (k < S.maxk) {
+            const double errkp1 = q.nrm[3] * S.ec[k];
+            temp = 1.4 * pow(errkp1 / S.rtol, 1.0 / (k + 2));
+            const double hkp1 = temp > 0.1 ? h / temp : 10.0 * h;
+            if (hkp1 > hopt) {
+                hopt = hkp1;
+                kopt = k + 1;
+            }
+        }
+        if (hopt > h) {
+            S.h = hopt;
+            if (kopt != k) {
+                S.order = kopt;
+                S.nconhk = 0;
+            }
+        }
+    }
+    if (S.info) {
+        sphnse_step_info& I = S.info[S.done];
+        I.t = S.t;
+        I.h = h;
+        I.err = err;
+        I.order = k;
+        I.newton_iters = S.newton_total;
+        I.rejections = S.rejections;
+        I.rhs_evals = S.rhs_evals;
+        I.next_order = S.order;
+        I.next_h = S.h;
+        I.h_dif_before = S.h_dif_before;
+    }
+    ++S.done;
+    S.attempt = 0;
 }
 
 inline double d2u_max(unsigned long long v) {
@@ -104,15 +313,13 @@ __global__ void k_wnorm(const double2* v, const double2* y, double thr, unsigned
     block_amax<1>(slots, r, id);
 }
 
-__global__ void k_rescale(double2* dif, Mat A, int k, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void rescale_entry(double2* dif, const double* A, int k, int n, int i) {
     double2 old[SPHNSE_MAXK];
     for (int j = 0; j < k; ++j) old[j] = dif[size_t(j) * n + i];
     for (int j = 0; j < k; ++j) {
         double sx = 0.0, sy = 0.0;
         for (int l = 0; l < k; ++l) {
-            const double a = A.a[l * SPHNSE_MAXK + j];
+            const double a = A[l * SPHNSE_MAXK + j];
             sx += a * old[l].x;
             sy += a * old[l].y;
         }
@@ -120,11 +327,17 @@ __global__ void k_rescale(double2* dif, Mat A, int k, int n) {
     }
 }
 
+__global__ void k_rescale(double2* dif, Mat A, int k, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rescale_entry(dif, A.a, k, n, i);
+}
+
 // y0 = y + sum_{j<k} D_j,  psi = sum_{j<k} g_j D_j,  d = 0,  ynew = y0
 // and slot 4 = ||y / max(|y|, thr)||_inf, the scale of the corrector's
 // rounding-level stop (FP32, like the corrector's other norms)
-__global__ void k_predict(const double2* y, const double2* dif, Coef g, int k, double2* y0, double2* psi,
-                          double2* d, double2* ynew, float thr, unsigned long long* slots, int n) {
+__device__ __forceinline__ void predict_block(const double2* y, const double2* dif, const double* g, int k,
+                                              double2* y0, double2* psi, double2* d, double2* ynew, float thr,
+                                              unsigned long long* slots, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float r[1] = {0.f};
     if (i < n) {
@@ -134,8 +347,8 @@ __global__ void k_predict(const double2* y, const double2* dif, Coef g, int k, d
             const double2 dj = dif[size_t(j) * n + i];
             a.x += dj.x;
             a.y += dj.y;
-            p.x += g.c[j] * dj.x;
-            p.y += g.c[j] * dj.y;
+            p.x += g[j] * dj.x;
+            p.y += g[j] * dj.y;
         }
         y0[i] = a;
         ynew[i] = a;
@@ -146,6 +359,11 @@ __global__ void k_predict(const double2* y, const double2* dif, Coef g, int k, d
     }
     const int id[1] = {4};
     block_amax_f<1>(slots, r, id, false);
+}
+
+__global__ void k_predict(const double2* y, const double2* dif, Coef g, int k, double2* y0, double2* psi,
+                          double2* d, double2* ynew, float thr, unsigned long long* slots, int n) {
+    predict_block(y, dif, g.c, k, y0, psi, d, ynew, thr, slots, n);
 }
 
 // One simplified-Newton update: r = c F - (psi + d), dl = r / (1 - c J_d),
@@ -194,65 +412,21 @@ __global__ void k_newton_g(const double2* F, const double2* y, const double2* y0
     block_amax_f<4>(slot, nv, id, bad);
 }
 
-// One thread: the corrector's stopping rule after iteration ctl->it (the same
-// tests as the host loop), then clear the slots the next iteration fills and
-// set the WHILE condition (0: stop).
+// One thread: the corrector's stopping rule after iteration ctl->it, then
+// clear the slots the next iteration fills and set the WHILE condition (0: stop).
 __global__ void k_newton_ctl(NewtonCtl* ctl, unsigned long long* slots, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double eps = 2.220446049250313e-16;
-    const int it = ctl->it;
-    bool stop = false, conv = false;
-    if (slots[7]) {
-        ctl->nonfinite = 1;
-        stop = true;
-    } else {
-        double nv[4];
-        for (int q = 0; q < 4; ++q) nv[q] = __longlong_as_double(static_cast<long long>(slots[q]));
-        if (it == 0) ctl->ynorm = __longlong_as_double(static_cast<long long>(slots[4]));
-        ctl->its = it + 1;
-        for (int q = 0; q < 4; ++q) ctl->nrm[q] = nv[q];
-        const double newnrm = nv[0], minnrm = 100.0 * eps * ctl->ynorm, oldnrm = ctl->oldnrm;
-        const double rtol = ctl->rtol;
-        if (ctl->tight) {
-            const bool stalled = !ctl->fp64 && it >= 3 && newnrm > 0.8 * oldnrm;
-            if (newnrm <= fmax(minnrm, 1e-15) || stalled) stop = conv = true;
-        } else if (newnrm <= minnrm) {
-            stop = conv = true;
-        } else if (it == 0) {
-            if (ctl->havrate) {
-                const double errit = newnrm * ctl->rate / (1.0 - ctl->rate);
-                if (errit <= 0.05 * rtol) stop = conv = true;
-            } else {
-                ctl->rate = 0.0;
-            }
-        } else if (newnrm > 0.9 * oldnrm) {
-            stop = true;   // too slow
-        } else {
-            ctl->rate = fmax(0.9 * ctl->rate, newnrm / oldnrm);
-            ctl->havrate = 1;
-            const double errit = newnrm * ctl->rate / (1.0 - ctl->rate);
-            if (errit <= 0.5 * rtol) stop = conv = true;
-            else if (it == ctl->maxit - 1) stop = true;
-            else if (0.5 * rtol < errit * pow(ctl->rate, double(ctl->maxit - 1 - it))) stop = true;
-        }
-        ctl->oldnrm = newnrm;
-        if (!stop && it + 1 >= ctl->maxit) {
-            stop = true;
-            conv = ctl->tight != 0;   // the host loop: a tight loop that ran out counts as converged
-        }
-    }
-    ctl->it = it + 1;
-    ctl->conv = conv;
-    ctl->stop = stop;
+    double nv[5];
+    for (int q = 0; q < 5; ++q) nv[q] = __longlong_as_double(static_cast<long long>(slots[q]));
+    const bool stop = newton_control(*ctl, nv, slots[7] != 0ull);
     for (int q = 0; q < 4; ++q) slots[q] = 0ull;
     slots[7] = 0ull;
     cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
 // D_{k+1} = d - D_k; D_k = d; D_j += D_{j+1} (j = k-1..0); y = ynew
-__global__ void k_accept(double2* dif, const double2* d, double2* y, const double2* ynew, int k, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void accept_entry(double2* dif, const double2* d, double2* y, const double2* ynew, int k,
+                                             int n, int i) {
     const double2 dd = d[i], dk = dif[size_t(k) * n + i];
     dif[size_t(k + 1) * n + i] = make_double2(dd.x - dk.x, dd.y - dk.y);
     double2 up = dd;
@@ -265,6 +439,50 @@ __global__ void k_accept(double2* dif, const double2* d, double2* y, const doubl
         up = v;
     }
     y[i] = ynew[i];
+}
+
+__global__ void k_accept(double2* dif, const double2* d, double2* y, const double2* ynew, int k, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) accept_entry(dif, d, y, ynew, k, n, i);
+}
+
+// The step loop's kernels.  Per attempt: k_prepare (the previous attempt's
+// accept if it was accepted, the rescale to this attempt's h, the predictor;
+// all three per entry), the Newton loop, k_step_next (one thread).  The loop
+// is entered through k_step_begin and left through k_accept_g.
+
+// one thread: the first attempt's parameters; clear the norm slots
+__global__ void k_step_begin(StepCtl* S, unsigned long long* slots) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    att_begin(*S);
+    for (int q = 0; q < 8; ++q) slots[q] = 0ull;
+}
+
+__global__ void k_prepare(double2* y, double2* dif, double2* y0, double2* psi, double2* d, double2* ynew,
+                          const StepCtl* S, unsigned long long* slots, cudaGraphConditionalHandle newton, int n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(newton, 1u);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        if (S->accept) accept_entry(dif, d, y, ynew, S->k_acc, n, i);
+        if (S->do_rescale) rescale_entry(dif, S->A, S->k, n, i);
+    }
+    predict_block(y, dif, S->g, S->k, y0, psi, d, ynew, fmaxf(float(S->thr), 1e-30f), slots, n);
+}
+
+// one thread: finish the attempt, start the next one if the loop goes on
+__global__ void k_step_next(StepCtl* S, unsigned long long* slots, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    att_end(*S);
+    const bool more = S->status == SPHNSE_OK && S->done < S->nsteps;
+    if (more) att_begin(*S);
+    for (int q = 0; q < 8; ++q) slots[q] = 0ull;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
+// the last attempt's accept, after the loop
+__global__ void k_accept_g(double2* dif, const double2* d, double2* y, const double2* ynew, const StepCtl* S, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && S->accept) accept_entry(dif, d, y, ynew, S->k_acc, n, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -483,6 +701,18 @@ int read_norms(sphnse_plan* P, double* out, int cnt) {
     return SPHNSE_OK;
 }
 
+// the five slots a Newton iteration reads, and whether a non-finite value was seen
+int read_newton_norms(sphnse_plan* P, double* nv, bool* bad) {
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(P->h_norms);
+    if (cudaMemcpyAsync(h, P->d_norms, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, P->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess)
+        return SPHNSE_E_CUDA;
+    *bad = h[7] != 0ull;
+    for (int i = 0; i < 5; ++i) nv[i] = d2u_max(h[i]);
+    return SPHNSE_OK;
+}
+
 int clear_norms(sphnse_plan* P) {
     return cudaMemsetAsync(P->d_norms, 0, 8 * sizeof(unsigned long long), P->stream) == cudaSuccess
                ? SPHNSE_OK
@@ -590,122 +820,52 @@ bool newton_graph_ready(sphnse_plan* P, sphnse_state* st, const double* forcing)
     return true;
 }
 
-// Predictor + simplified Newton.  tight: iterate until the update norm is
-// below max(minnrm, 1e-15) (replay).  Returns SPHNSE_OK / error; *conv set.
-int corrector(sphnse_plan* P, sphnse_state* st, const double* forcing, double h, int k, bool tight, int maxit,
-              const NDFConst& C, bool* conv, int* its, double norms[4]) {
+// Predictor (weights g) + simplified Newton with the parameters in q; the
+// results (convergence, iterations, norms, rate memory) come back in q.  The
+// iterations run as one graph launch when the Newton graph is available, else
+// one by one from the host with the same stopping rule.
+int corrector(sphnse_plan* P, sphnse_state* st, const double* forcing, const double* g, NewtonCtl& q) {
     const int n = P->n_coeff;
     Work W = work(P);
-    const double thr = P->atol / P->rtol;
-    if (h != st->miter_h || k != st->miter_k) {
-        st->havrate = 0;
-        st->miter_h = h;
-        st->miter_k = k;
-    }
-    Coef g;
-    for (int j = 0; j < SPHNSE_MAXK; ++j) g.c[j] = j < k ? C.gamma[j] * C.iga[k - 1] : 0.0;
+    Coef gc;
+    for (int j = 0; j < SPHNSE_MAXK; ++j) gc.c[j] = g[j];
     int rc;
     if ((rc = clear_norms(P))) return rc;
     stage_begin(P, SPHNSE_STAGE_STEP);
     k_predict<<<grid(n), 256, 0, P->stream>>>(reinterpret_cast<const double2*>(st->alpha),
-                                               reinterpret_cast<const double2*>(st->dif), g, k, W.y0, W.psi, W.d,
-                                               W.ynew, fmaxf(float(thr), 1e-30f), P->d_norms, n);
+                                               reinterpret_cast<const double2*>(st->dif), gc, q.k, W.y0, W.psi, W.d,
+                                               W.ynew, fmaxf(float(q.thr), 1e-30f), P->d_norms, n);
     stage_end(P, SPHNSE_STAGE_STEP);
     if ((rc = stage_launch_check(P))) return rc;
-    const double cc = h * C.iga[k - 1];
     if (newton_graph_ready(P, st, forcing)) {
-        NewtonCtl& q = *P->h_ctl;
-        std::memset(&q, 0, sizeof(q));
-        q.c = cc;
-        q.nu = P->nu;
-        q.omega = P->Omega;
-        q.thr = thr;
-        q.rtol = P->rtol;
-        q.rate = st->rate;
-        q.havrate = st->havrate;
-        q.k = k;
-        q.maxit = maxit;
-        q.tight = tight;
-        q.fp64 = P->precision == SPHNSE_FP64;
+        *P->h_ctl = q;
         if (cudaMemcpyAsync(P->d_ctl, P->h_ctl, sizeof(NewtonCtl), cudaMemcpyHostToDevice, P->stream) != cudaSuccess ||
             cudaGraphLaunch(P->ng_exec, P->stream) != cudaSuccess ||
             cudaMemcpyAsync(P->h_ctl, P->d_ctl, sizeof(NewtonCtl), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
             cudaStreamSynchronize(P->stream) != cudaSuccess)
             return SPHNSE_E_CUDA;
-        if (q.nonfinite) return SPHNSE_E_NONFINITE;
-        *conv = q.conv != 0;
-        *its = q.its;
-        for (int j = 0; j < 4; ++j) norms[j] = q.nrm[j];
-        st->rate = q.rate;
-        st->havrate = q.havrate;
+        q = *P->h_ctl;
         return SPHNSE_OK;
     }
-    const double eps = 2.220446049250313e-16;
-    double oldnrm = 0.0, ynorm = 0.0;
-    *conv = false;
-    for (int it = 0; it < maxit; ++it) {
+    const int k = q.k;
+    for (;;) {
         if ((rc = rhs_device(P, reinterpret_cast<const double*>(W.ynew), forcing,
                              reinterpret_cast<double*>(W.F))))
             return rc;
-        if (it > 0 && (rc = clear_norms(P))) return rc;
+        if (q.it > 0 && (rc = clear_norms(P))) return rc;
         stage_begin(P, SPHNSE_STAGE_STEP);
         k_newton<<<grid(n), 256, 0, P->stream>>>(
             W.F, reinterpret_cast<const double2*>(st->alpha), W.y0, W.psi, W.d, W.ynew,
             k >= 2 ? reinterpret_cast<const double2*>(st->dif) + size_t(k - 1) * n : nullptr,
-            reinterpret_cast<const double2*>(st->dif) + size_t(k) * n, P->d_lm, cc, P->nu, P->Omega, thr,
+            reinterpret_cast<const double2*>(st->dif) + size_t(k) * n, P->d_lm, q.c, q.nu, q.omega, q.thr,
             P->d_norms, n);
         stage_end(P, SPHNSE_STAGE_STEP);
         if ((rc = stage_launch_check(P))) return rc;
         double nv[5];
-        if ((rc = read_norms(P, nv, it == 0 ? 5 : 4))) return rc;
-        if (it == 0) ynorm = nv[4];
-        *its = it + 1;
-        for (int q = 0; q < 4; ++q) norms[q] = nv[q];
-        const double newnrm = nv[0];
-        const double minnrm = 100.0 * eps * ynorm;
-        if (tight) {
-            // converged to the rounding level: below 1e-15 in the weighted
-            // norm, or no longer shrinking (FP32 / BF16 contractions stall at
-            // their own rounding level long before 1e-15)
-            const bool stalled = P->precision != SPHNSE_FP64 && it >= 3 && newnrm > 0.8 * oldnrm;
-            if (newnrm <= std::max(minnrm, 1e-15) || stalled) {
-                *conv = true;
-                return SPHNSE_OK;
-            }
-            oldnrm = newnrm;
-            continue;
-        }
-        if (newnrm <= minnrm) {
-            *conv = true;
-            return SPHNSE_OK;
-        }
-        if (it == 0) {
-            if (st->havrate) {
-                const double errit = newnrm * st->rate / (1.0 - st->rate);
-                if (errit <= 0.05 * P->rtol) {
-                    *conv = true;
-                    return SPHNSE_OK;
-                }
-            } else {
-                st->rate = 0.0;
-            }
-        } else if (newnrm > 0.9 * oldnrm) {
-            return SPHNSE_OK;  // too slow
-        } else {
-            st->rate = std::max(0.9 * st->rate, newnrm / oldnrm);
-            st->havrate = 1;
-            const double errit = newnrm * st->rate / (1.0 - st->rate);
-            if (errit <= 0.5 * P->rtol) {
-                *conv = true;
-                return SPHNSE_OK;
-            }
-            if (it == maxit - 1) return SPHNSE_OK;
-            if (0.5 * P->rtol < errit * std::pow(st->rate, maxit - 1 - it)) return SPHNSE_OK;
-        }
-        oldnrm = newnrm;
+        bool bad;
+        if ((rc = read_newton_norms(P, nv, &bad))) return rc;
+        if (newton_control(q, nv, bad)) return SPHNSE_OK;
     }
-    if (tight) *conv = true;
-    return SPHNSE_OK;
 }
 
 int accept(sphnse_plan* P, sphnse_state* st, int k) {
@@ -716,6 +876,208 @@ int accept(sphnse_plan* P, sphnse_state* st, int k) {
                                                       P->n_coeff);
     stage_end(P, SPHNSE_STAGE_STEP);
     return stage_launch_check(P);
+}
+
+// The controller's inputs and memory for nsteps steps from st.
+void ctl_load(const sphnse_plan* P, const sphnse_state* st, int nsteps, sphnse_step_info* info, StepCtl& S) {
+    const NDFConst C(P->bdf != 0);
+    S = StepCtl{};
+    S.rtol = P->rtol;
+    S.thr = P->atol / P->rtol;
+    S.h_max = P->h_max;
+    S.maxk = P->max_order;
+    S.newton_max = P->newton_max;
+    S.fp64 = P->precision == SPHNSE_FP64;
+    S.nsteps = nsteps;
+    S.nu = P->nu;
+    S.omega = P->Omega;
+    for (int j = 0; j < SPHNSE_MAXK; ++j) {
+        S.gamma[j] = C.gamma[j];
+        S.iga[j] = C.iga[j];
+        S.ec[j] = C.ec[j];
+    }
+    S.info = info;
+    S.t = st->t;
+    S.h = st->h;
+    S.t_end = st->t_end;
+    S.h_dif = st->h_dif;
+    S.rate = st->rate;
+    S.miter_h = st->miter_h;
+    S.order = st->order;
+    S.nconhk = st->nconhk;
+    S.havrate = st->havrate;
+    S.miter_k = st->miter_k;
+    S.status = SPHNSE_OK;
+}
+
+void ctl_store(const StepCtl& S, sphnse_state* st) {
+    st->t = S.t;
+    st->h = S.h;
+    st->h_dif = S.h_dif;
+    st->rate = S.rate;
+    st->miter_h = S.miter_h;
+    st->order = S.order;
+    st->nconhk = S.nconhk;
+    st->havrate = S.havrate;
+    st->miter_k = S.miter_k;
+}
+
+// nsteps steps with the attempts driven from the host (stage timing on, or no
+// step graph): the same controller functions as the device loop.
+int steps_host(sphnse_plan* P, sphnse_state* st, const double* forcing, int nsteps, sphnse_step_info* info) {
+    StepCtl S;
+    ctl_load(P, st, nsteps, info, S);
+    int rc = SPHNSE_OK;
+    while (S.status == SPHNSE_OK && S.done < S.nsteps) {
+        att_begin(S);
+        if (S.do_rescale) {
+            Mat A;
+            std::memcpy(A.a, S.A, sizeof(A.a));
+            stage_begin(P, SPHNSE_STAGE_STEP);
+            k_rescale<<<grid(P->n_coeff), 256, 0, P->stream>>>(reinterpret_cast<double2*>(st->dif), A, S.k,
+                                                               P->n_coeff);
+            stage_end(P, SPHNSE_STAGE_STEP);
+            if ((rc = stage_launch_check(P))) break;
+        }
+        if ((rc = corrector(P, st, forcing, S.g, S.nc))) break;
+        att_end(S);
+        if (S.accept && (rc = accept(P, st, S.k))) break;
+    }
+    ctl_store(S, st);
+    return rc ? rc : S.status;
+}
+
+// The whole step loop as one graph: k_step_begin, then a WHILE node over
+// attempts whose body is k_prepare, the Newton WHILE node (RHS, update,
+// stopping rule) and k_step_next, then k_accept_g.  The loop ends on the
+// device after nsteps accepted steps or an error.  Built per (state,
+// forcing, precision, nu, Omega); any failure to build leaves the host loop
+// in charge.
+bool step_graph_ready(sphnse_plan* P, sphnse_state* st, const double* forcing) {
+    if (P->sg_failed || P->timing) return false;
+    const void* key[4] = {st->alpha, st->dif, forcing,
+                          reinterpret_cast<const void*>(uintptr_t(P->precision) | (uintptr_t(P->coriolis_split) << 8))};
+    if (P->sg_exec && std::equal(key, key + 4, P->sg_key) && P->sg_nu == P->nu && P->sg_omega == P->Omega) return true;
+    if (P->sg_exec) {
+        cudaGraphExecDestroy(P->sg_exec);
+        P->sg_exec = nullptr;
+    }
+    if ((!P->d_step && (cudaMalloc(reinterpret_cast<void**>(&P->d_step), sizeof(StepCtl)) != cudaSuccess ||
+                        cudaMallocHost(reinterpret_cast<void**>(&P->h_step), sizeof(StepCtl)) != cudaSuccess)) ||
+        (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess)) {
+        cudaGetLastError();
+        P->sg_failed = true;
+        return false;
+    }
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return false;
+    Work W = work(P);
+    const int n = P->n_coeff;
+    double2* alpha = reinterpret_cast<double2*>(st->alpha);
+    double2* dif = reinterpret_cast<double2*>(st->dif);
+    const cudaStream_t cs = P->cap_stream;
+    // add a conditional WHILE node to the graph under capture on cs, make it
+    // the capture's only dependency and return its body graph (null on failure)
+    auto add_while = [cs](cudaGraphConditionalHandle h) -> cudaGraph_t {
+        cudaStreamCaptureStatus status;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        if (cudaStreamGetCaptureInfo(cs, &status, nullptr, &capg, &deps, nullptr, &ndeps) != cudaSuccess ||
+            status != cudaStreamCaptureStatusActive)
+            return nullptr;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, capg, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+            return nullptr;
+        return cp.conditional.phGraph_out[0];
+    };
+    auto begin = [cs](cudaGraph_t gr) {
+        return gr && cudaStreamBeginCaptureToGraph(cs, gr, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+                         cudaSuccess;
+    };
+    auto end = [cs]() {
+        cudaGraph_t out = nullptr;
+        return cudaStreamEndCapture(cs, &out) == cudaSuccess;
+    };
+    const cudaStream_t saved = P->stream;
+    P->stream = cs;
+    cudaGraph_t g = nullptr, body = nullptr, inner = nullptr;
+    cudaGraphConditionalHandle hloop, hnewton;
+    // the top level: begin, the attempt loop, the last accept
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&hloop, g, 1, cudaGraphCondAssignDefault) == cudaSuccess && begin(g);
+    if (ok) {
+        k_step_begin<<<1, 32, 0, cs>>>(P->d_step, P->d_norms);
+        body = add_while(hloop);
+        k_accept_g<<<grid(n), 256, 0, cs>>>(dif, W.d, alpha, W.ynew, P->d_step, n);
+        ok = end() && body;
+    }
+    // one attempt: prepare, the Newton loop, the controller
+    ok = ok && cudaGraphConditionalHandleCreate(&hnewton, body, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+         begin(body);
+    if (ok) {
+        k_prepare<<<grid(n), 256, 0, cs>>>(alpha, dif, W.y0, W.psi, W.d, W.ynew, P->d_step, P->d_norms, hnewton, n);
+        inner = add_while(hnewton);
+        k_step_next<<<1, 32, 0, cs>>>(P->d_step, P->d_norms, hloop);
+        ok = end() && inner;
+    }
+    // one Newton iteration: RHS at ynew, update, stopping rule
+    ok = ok && begin(inner);
+    if (ok) {
+        const int rc = rhs_device(P, reinterpret_cast<const double*>(W.ynew), forcing, reinterpret_cast<double*>(W.F));
+        k_newton_g<<<grid(n), 256, 0, cs>>>(W.F, alpha, W.y0, W.psi, W.d, W.ynew, dif, P->d_lm, &P->d_step->nc,
+                                            P->d_norms, n);
+        k_newton_ctl<<<1, 32, 0, cs>>>(&P->d_step->nc, P->d_norms, hnewton);
+        ok = end() && rc == SPHNSE_OK;
+    }
+    P->stream = saved;
+    if (ok) ok = cudaGraphInstantiate(&P->sg_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves no sticky error; clear the last one
+    if (!ok) {
+        P->sg_exec = nullptr;
+        P->sg_failed = true;
+        return false;
+    }
+    std::copy(key, key + 4, P->sg_key);
+    P->sg_nu = P->nu;
+    P->sg_omega = P->Omega;
+    return true;
+}
+
+// nsteps steps in one launch of the step graph: the controller's state goes
+// up before and comes back after it (one host synchronisation per call).
+int steps_graph(sphnse_plan* P, sphnse_state* st, int nsteps, sphnse_step_info* info) {
+    if (info && nsteps > P->info_cap) {
+        if (P->d_info) cudaFree(P->d_info);
+        if (P->h_info) cudaFreeHost(P->h_info);
+        P->d_info = P->h_info = nullptr;
+        P->info_cap = 0;
+        const size_t bytes = size_t(nsteps) * sizeof(sphnse_step_info);
+        if (cudaMalloc(reinterpret_cast<void**>(&P->d_info), bytes) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&P->h_info), bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return SPHNSE_E_NOMEM;
+        }
+        P->info_cap = nsteps;
+    }
+    StepCtl& S = *P->h_step;
+    ctl_load(P, st, nsteps, info ? P->d_info : nullptr, S);
+    if (cudaMemcpyAsync(P->d_step, P->h_step, sizeof(StepCtl), cudaMemcpyHostToDevice, P->stream) != cudaSuccess ||
+        cudaGraphLaunch(P->sg_exec, P->stream) != cudaSuccess ||
+        cudaMemcpyAsync(P->h_step, P->d_step, sizeof(StepCtl), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess ||
+        (info && cudaMemcpyAsync(P->h_info, P->d_info, size_t(nsteps) * sizeof(sphnse_step_info),
+                                 cudaMemcpyDeviceToHost, P->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess)
+        return SPHNSE_E_CUDA;
+    ctl_store(S, st);
+    if (info) std::memcpy(info, P->h_info, size_t(S.done) * sizeof(sphnse_step_info));   // entries of accepted steps
+    return S.status;
 }
 
 }  // namespace
@@ -757,112 +1119,14 @@ int sphnse_state_init(sphnse_plan* P, sphnse_state* st, double t0, double h0, co
 }
 
 int sphnse_step(sphnse_plan* P, sphnse_state* st, const double* forcing, sphnse_step_info* info) {
-    if (!P || !st || !st->alpha || !st->dif) return SPHNSE_E_ARG;
-    const NDFConst C(P->bdf != 0);
-    const int maxk = P->max_order;
-    bool nofailed = true;
-    int rejections = 0, newton_total = 0, rhs_evals = 0;
-    const double h_dif_before = st->h_dif;
-    const double eps16 = 16.0 * 2.220446049250313e-16;
-    int rc;
-    for (int attempt = 0; attempt < 200; ++attempt) {
-        const double hmin = eps16 * std::fabs(st->t);
-        double h = std::min(P->h_max, std::max(hmin, st->h));
-        if (1.1 * h >= st->t_end - st->t) h = st->t_end - st->t;
-        st->h = h;
-        int k = st->order;
-        if ((rc = rescale(P, st, h, k))) return rc;
-        bool conv;
-        int its = 0;
-        double nrm[4];
-        if ((rc = corrector(P, st, forcing, h, k, false, P->newton_max, C, &conv, &its, nrm))) return rc;
-        newton_total += its;
-        rhs_evals += its;
-        if (!conv) {
-            ++rejections;
-            if (h <= hmin) return SPHNSE_E_STEP_TOO_SMALL;
-            st->h = std::max(hmin, 0.3 * h);
-            continue;
-        }
-        const double err = nrm[1] * C.ec[k - 1];
-        if (err > P->rtol) {
-            ++rejections;
-            if (h <= hmin) return SPHNSE_E_STEP_TOO_SMALL;
-            if (nofailed) {
-                nofailed = false;
-                double hopt = h * std::max(0.1, 0.833 * std::pow(P->rtol / err, 1.0 / (k + 1)));
-                if (k > 1) {
-                    const double errkm1 = nrm[2] * C.ec[k - 2];
-                    const double hkm1 = h * std::max(0.1, 0.769 * std::pow(P->rtol / errkm1, 1.0 / k));
-                    if (hkm1 > hopt) {
-                        hopt = std::min(h, hkm1);
-                        st->order = k - 1;
-                    }
-                }
-                st->h = std::max(hmin, hopt);
-            } else {
-                st->h = std::max(hmin, 0.5 * h);
-            }
-            continue;
-        }
-        // accepted
-        if ((rc = accept(P, st, k))) return rc;
-        st->t += h;
-        st->nconhk = std::min(st->nconhk + 1, SPHNSE_MAXK + 2);
-        if (st->nconhk >= k + 2) {
-            double temp = 1.2 * std::pow(err / P->rtol, 1.0 / (k + 1));
-            double hopt = temp > 0.1 ? h / temp : 10.0 * h;
-            int kopt = k;
-            if (k > 1) {
-                const double errkm1 = nrm[2] * C.ec[k - 2];
-                temp = 1.3 * std::pow(errkm1 / P->rtol, 1.0 / k);
-                const double hkm1 = temp > 0.1 ? h / temp : 10.0 * h;
-                if (hkm1 > hopt) {
-                    hopt = hkm1;
-                    kopt = k - 1;
-                }
-            }
-            if (k < maxk) {
-                const double errkp1 = nrm[3] * C.ec[k];
-                temp = 1.4 * std::pow(errkp1 / P->rtol, 1.0 / (k + 2));
-                const double hkp1 = temp > 0.1 ? h / temp : 10.0 * h;
-                if (hkp1 > hopt) {
-                    hopt = hkp1;
-                    kopt = k + 1;
-                }
-            }
-            if (hopt > h) {
-                st->h = hopt;
-                if (kopt != k) {
-                    st->order = kopt;
-                    st->nconhk = 0;
-                }
-            }
-        }
-        if (info) {
-            info->t = st->t;
-            info->h = h;
-            info->err = err;
-            info->order = k;
-            info->newton_iters = newton_total;
-            info->rejections = rejections;
-            info->rhs_evals = rhs_evals;
-            info->next_order = st->order;
-            info->next_h = st->h;
-            info->h_dif_before = h_dif_before;
-        }
-        return SPHNSE_OK;
-    }
-    return SPHNSE_E_STEP_TOO_SMALL;
+    return sphnse_advance(P, st, forcing, 1, info);
 }
 
 int sphnse_advance(sphnse_plan* P, sphnse_state* st, const double* forcing, int nsteps, sphnse_step_info* info) {
-    if (!P || !st || nsteps < 0) return SPHNSE_E_ARG;
-    for (int s = 0; s < nsteps; ++s) {
-        const int rc = sphnse_step(P, st, forcing, info ? info + s : nullptr);
-        if (rc) return rc;
-    }
-    return SPHNSE_OK;
+    if (!P || !st || !st->alpha || !st->dif || nsteps < 0) return SPHNSE_E_ARG;
+    if (nsteps == 0) return SPHNSE_OK;
+    if (step_graph_ready(P, st, forcing)) return steps_graph(P, st, nsteps, info);
+    return steps_host(P, st, forcing, nsteps, info);
 }
 
 int sphnse_replay_step(sphnse_plan* P, sphnse_state* st, const double* forcing, double h, int k, int newton_max,
@@ -873,21 +1137,31 @@ int sphnse_replay_step(sphnse_plan* P, sphnse_state* st, const double* forcing, 
     st->order = k;
     int rc;
     if ((rc = rescale(P, st, h, k))) return rc;
-    bool conv;
-    int its = 0;
-    double nrm[4];
-    if ((rc = corrector(P, st, forcing, h, k, true, newton_max, C, &conv, &its, nrm))) return rc;
+    if (h != st->miter_h || k != st->miter_k) {
+        st->havrate = 0;
+        st->miter_h = h;
+        st->miter_k = k;
+    }
+    double g[SPHNSE_MAXK];
+    for (int j = 0; j < SPHNSE_MAXK; ++j) g[j] = j < k ? C.gamma[j] * C.iga[k - 1] : 0.0;
+    NewtonCtl q;
+    newton_init(q, h * C.iga[k - 1], P->nu, P->Omega, P->atol / P->rtol, P->rtol, st->rate, st->havrate, k,
+                newton_max, 1, P->precision == SPHNSE_FP64);
+    if ((rc = corrector(P, st, forcing, g, q))) return rc;
+    if (q.nonfinite) return SPHNSE_E_NONFINITE;
+    st->rate = q.rate;
+    st->havrate = q.havrate;
     if ((rc = accept(P, st, k))) return rc;
     st->t += h;
     st->h = h;
     if (info) {
         info->t = st->t;
         info->h = h;
-        info->err = nrm[1] * C.ec[k - 1];
+        info->err = q.nrm[1] * C.ec[k - 1];
         info->order = k;
-        info->newton_iters = its;
+        info->newton_iters = q.its;
         info->rejections = 0;
-        info->rhs_evals = its;
+        info->rhs_evals = q.its;
         info->next_order = k;
         info->next_h = h;
         info->h_dif_before = h_dif_before;

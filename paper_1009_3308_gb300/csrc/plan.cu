@@ -187,6 +187,11 @@ static void destroy_plan(sphnse_plan* P) {
     if (P->d_ctl) cudaFree(P->d_ctl);
     if (P->h_ctl) cudaFreeHost(P->h_ctl);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    if (P->sg_exec) cudaGraphExecDestroy(P->sg_exec);
+    if (P->d_step) cudaFree(P->d_step);
+    if (P->h_step) cudaFreeHost(P->h_step);
+    if (P->d_info) cudaFree(P->d_info);
+    if (P->h_info) cudaFreeHost(P->h_info);
     void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
                     P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_ftw, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
                     P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};
