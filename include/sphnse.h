@@ -332,10 +332,11 @@ int sphnse_ensemble_init(sphnse_ensemble* ens, double t0);
 int sphnse_ensemble_step(sphnse_ensemble* ens, sphnse_step_info* info);
 
 /* nsteps >= 0 accepted steps of every instance, each at its own pace: the
- * instances advance in rounds of one CUDA-graph launch (accept, rescale and
- * predictor where due, one batched RHS of all instances, one Newton update)
- * and one host read of their norms, so an instance never waits for another's
- * rejected attempts or Newton iterations.  Each instance follows exactly the
+ * instances advance in rounds (accept, rescale and predictor where due, one
+ * batched RHS of all instances, one Newton update, then the per-instance
+ * controllers on the device), all rounds in one CUDA-graph launch with a
+ * device-side loop condition, so an instance never waits for another's
+ * rejected attempts or Newton iterations and the host waits once per call.  Each instance follows exactly the
  * step/order sequence sphnse_step gives it alone.  info (host, n entries or
  * NULL): the last step's t, h, err, order, next_order, next_h, h_dif_before,
  * with newton_iters, rhs_evals and rejections summed over the call. */

@@ -16,9 +16,12 @@
 // previous step, rescale and predictor of a new attempt, one batched RHS and
 // one Newton update -- in which every instance does whatever its own
 // controller is at (flag bits in a per-instance parameter array), followed by
-// one read of all instances' norms.  An instance that converges, rejects or
-// accepts starts its next attempt in the next round, so no instance waits for
-// another's rejected attempts or extra Newton iterations.
+// a controller kernel (one thread per instance; the same host/device
+// functions as sphnse_step) that reads the instance's norms and sets its
+// flags for the next round.  The rounds are a WHILE node of one graph launch
+// per call, so the host waits once per call.  An instance that converges,
+// rejects or accepts starts its next attempt in the next round, so no
+// instance waits for another's rejected attempts or extra Newton iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +32,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "controller.cuh"
 #include "dmath.cuh"
 #include "newton.cuh"
 #include "reduce.cuh"
@@ -36,8 +40,6 @@
 namespace sph {
 namespace {
 
-constexpr double EPS = 2.220446049250313e-16;
-const double KAPPA_E[SPHNSE_MAXK] = {-0.1850, -1.0 / 9.0, -0.0823, -0.0415, 0.0};
 
 // flag bits of InstPar::flags: what an instance does in the current launch
 constexpr int F_INIT = 1;       // initial weight norm of F and zeroed differences
@@ -180,48 +182,121 @@ __global__ void kb_accept(const int2* btab, const InstPar* par, double2* dif, co
     y[o + i] = ynew[o + i];
 }
 
-// (R(rho) U)[:k, :k]
-void rescale_mat(int k, double rho, double* A) {
-    double R[SPHNSE_MAXK][SPHNSE_MAXK], U[SPHNSE_MAXK][SPHNSE_MAXK];
-    for (int j = 1; j <= k; ++j) {
-        double r = 1.0, u = 1.0;
-        for (int i = 1; i <= k; ++i) {
-            r *= (i - 1.0 - j * rho) / i;
-            u *= (i - 1.0 - j) / i;
-            R[i - 1][j - 1] = r;
-            U[i - 1][j - 1] = u;
-        }
-    }
-    std::memset(A, 0, sizeof(double) * SPHNSE_MAXK * SPHNSE_MAXK);
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) {
-            double s = 0.0;
-            for (int l = 0; l < k; ++l) s += R[i][l] * U[l][j];
-            A[i * SPHNSE_MAXK + j] = s;
-        }
-}
-
-struct Ctl {
-    double t = 0, h = 0, h_dif = 0, rate = 0, miter_h = 0;
-    int k = 1, nconhk = 0, havrate = 0, miter_k = 0;
-    // per step
-    bool done = false, nofailed = true;
-    int rejections = 0, newton = 0;
-    double h_dif_before = 0, hmin = 0, ha = 0;
-    int ka = 1;
-    // per attempt
-    bool attempting = false, in_newton = false, conv = false;
-    int its = 0;
-    double oldnrm = 0, ynorm = 0, nrm[4] = {0, 0, 0, 0};
-    // asynchronous rounds
-    int state = 0;                // S_IDLE, S_START (new attempt next round), S_NEWTON
-    int it = 0;                   // Newton iteration of the current attempt
-    int steps_left = 0, attempts = 0;
-    bool pending_accept = false;  // F_ACCEPT in the next launch
-    int acc_k = 1;
+// Per-call inputs and results of the device round loop.
+struct EnsLoop {
+    double rtol, thr, h_max;
+    int nsteps, maxk, newton_max;
+    int status, rounds, max_rounds;
+    int active;          // some instance has a Newton update next round (controller blocks)
+    unsigned arrived;    // controller blocks done with the current round
 };
 
-constexpr int S_IDLE = 0, S_START = 1, S_NEWTON = 2;
+// One block, a thread per instance (strided): open a call of nsteps steps.
+__global__ void kb_call_begin(StepCtl* sc, InstPar* par, unsigned long long* norms, EnsLoop* L, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        StepCtl& S = sc[i];
+        S.rtol = L->rtol;
+        S.thr = L->thr;
+        S.h_max = L->h_max;
+        S.maxk = L->maxk;
+        S.newton_max = L->newton_max;
+        S.nsteps = L->nsteps;
+        S.done = 0;
+        S.attempt = 0;
+        S.status = SPHNSE_OK;
+        S.sum_newton = 0;
+        S.sum_rejections = 0;
+        S.accept = 0;
+        S.phase = L->nsteps > 0 ? 1 : 0;
+        par[i].flags = 0;
+        for (int q = 0; q < 8; ++q) norms[8 * size_t(i) + q] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        L->status = SPHNSE_OK;
+        L->rounds = 0;
+        L->active = 0;
+        L->arrived = 0u;
+    }
+}
+
+// A thread per instance, one warp per block (the controller is FP64 work, so
+// it is spread over SMs): take the results of the round just run (Newton
+// stopping rule; at the end of an attempt rejection or acceptance and the
+// next order and step size), set each instance's flags and parameters for
+// the next round and clear its norm slots.  The last block to finish
+// continues the loop while some instance still has a Newton update to do.
+// counted: this call ends a round (not the set-up call before the first).
+constexpr int CTL_THREADS = 32;
+
+__global__ void kb_round_ctl(StepCtl* sc, InstPar* par, unsigned long long* norms, sphnse_step_info* info,
+                             EnsLoop* L, int n, int counted, cudaGraphConditionalHandle loop) {
+    bool active = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        StepCtl& S = sc[i];
+        InstPar& p = par[i];
+        unsigned long long* nr = norms + 8 * size_t(i);
+        if (p.flags & F_NEWTON) {
+            double nv[5];
+            for (int q = 0; q < 5; ++q) nv[q] = __longlong_as_double(static_cast<long long>(nr[q]));
+            if (newton_control(S.nc, nv, nr[7] != 0ull)) {
+                att_end(S);
+                if (S.status != SPHNSE_OK) {
+                    atomicCAS(&L->status, SPHNSE_OK, S.status);
+                    S.phase = 0;
+                } else {
+                    if (S.accept) {
+                        // the last accepted step, with the call's totals
+                        sphnse_step_info& I = info[i];
+                        fill_info(S, I);
+                        I.newton_iters = I.rhs_evals = S.sum_newton;
+                        I.rejections = S.sum_rejections;
+                    }
+                    S.phase = S.done < S.nsteps ? 1 : 0;
+                }
+            }
+        }
+        int flags = 0;
+        if (S.accept) {
+            flags |= F_ACCEPT;
+            p.ka = S.k_acc;
+            S.accept = 0;
+        }
+        if (S.phase == 1) {
+            att_begin(S);
+            if (S.do_rescale) {
+                flags |= F_RESCALE;
+                for (int q = 0; q < SPHNSE_MAXK * SPHNSE_MAXK; ++q) p.A[q] = S.A[q];
+            }
+            flags |= F_PREDICT | F_NEWTON;
+            p.k = S.k;
+            p.c = S.nc.c;
+            p.thr = S.thr;
+            for (int q = 0; q < SPHNSE_MAXK; ++q) p.g[q] = S.g[q];
+            S.phase = 2;
+        } else if (S.phase == 2) {
+            flags |= F_NEWTON;
+        }
+        p.flags = flags;
+        for (int q = 0; q < 8; ++q) nr[q] = 0ull;
+        active = active || (flags & F_NEWTON);
+    }
+    active = __syncthreads_or(active);
+    if (threadIdx.x != 0) return;
+    if (active) atomicOr(&L->active, 1);
+    __threadfence();
+    if (atomicAdd(&L->arrived, 1u) != gridDim.x - 1) return;
+    // the last block: every block's flags and errors are visible
+    __threadfence();
+    const bool any = atomicExch(&L->active, 0) != 0;
+    L->arrived = 0u;
+    if (counted) ++L->rounds;
+    int status = atomicAdd(&L->status, 0);
+    // every round advances a Newton iteration, an attempt or a step of each
+    // active instance, so the loop ends by itself; the cap only guards
+    // against a controller fault
+    if (any && status == SPHNSE_OK && L->rounds >= L->max_rounds) status = L->status = SPHNSE_E_STEP_TOO_SMALL;
+    cudaGraphSetConditional(loop, any && status == SPHNSE_OK ? 1u : 0u);
+}
 
 struct Bucket {
     int L = 0, nb = 0;
@@ -267,8 +342,12 @@ struct sphnse_ensemble {
     int nbt = 0;
     unsigned long long* d_norms = nullptr;
     unsigned long long* h_norms = nullptr;
-    std::vector<Ctl> ctl;
-    cudaGraphExec_t g_rhs_alpha = nullptr, g_round = nullptr;
+    StepCtl* d_sc = nullptr;         // per-instance controller state (device resident)
+    EnsLoop* d_loop = nullptr;
+    EnsLoop* h_loop = nullptr;       // pinned
+    sphnse_step_info* d_info = nullptr;
+    sphnse_step_info* h_info = nullptr;  // pinned
+    cudaGraphExec_t g_rhs_alpha = nullptr, g_adv = nullptr;
     int max_n = 0;
     long rounds = 0;                 // graph launches of the last advance
 };
@@ -349,7 +428,7 @@ void destroy_ens(sphnse_ensemble* E) {
     if (E->stream) cudaStreamSynchronize(E->stream);
     else cudaDeviceSynchronize();
     if (E->g_rhs_alpha) cudaGraphExecDestroy(E->g_rhs_alpha);
-    if (E->g_round) cudaGraphExecDestroy(E->g_round);
+    if (E->g_adv) cudaGraphExecDestroy(E->g_adv);
     if (E->par) cudaFreeHost(E->par);
     if (E->d_btab) cudaFree(E->d_btab);
     if (E->ev_in) cudaEventDestroy(E->ev_in);
@@ -362,10 +441,13 @@ void destroy_ens(sphnse_ensemble* E) {
         tc_batch_ana_free(&B.tca);
         if (B.P) sphnse_plan_destroy(B.P);
     }
-    void* ptrs[] = {E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew, E->F, E->d_par, E->d_norms};
+    void* ptrs[] = {E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew, E->F, E->d_par, E->d_norms, E->d_sc,
+                    E->d_loop, E->d_info};
     for (void* q : ptrs)
         if (q) cudaFree(q);
-    if (E->h_norms) cudaFreeHost(E->h_norms);
+    void* hptrs[] = {E->h_norms, E->h_loop, E->h_info};
+    for (void* q : hptrs)
+        if (q) cudaFreeHost(q);
     if (E->stream) cudaStreamDestroy(E->stream);
     delete E;
 }
@@ -509,6 +591,13 @@ sphnse_ensemble* sphnse_ensemble_create(int n, const int* Ls, const double* nus,
         rc = SPHNSE_E_NOMEM;
     if (!rc && cudaMallocHost(reinterpret_cast<void**>(&E->par), size_t(n) * sizeof(InstPar)) != cudaSuccess)
         rc = SPHNSE_E_NOMEM;
+    if (!rc && (cudaMalloc(reinterpret_cast<void**>(&E->d_sc), size_t(n) * sizeof(StepCtl)) != cudaSuccess ||
+                cudaMalloc(reinterpret_cast<void**>(&E->d_loop), sizeof(EnsLoop)) != cudaSuccess ||
+                cudaMallocHost(reinterpret_cast<void**>(&E->h_loop), sizeof(EnsLoop)) != cudaSuccess ||
+                cudaMalloc(reinterpret_cast<void**>(&E->d_info), size_t(n) * sizeof(sphnse_step_info)) != cudaSuccess ||
+                cudaMallocHost(reinterpret_cast<void**>(&E->h_info), size_t(n) * sizeof(sphnse_step_info)) !=
+                    cudaSuccess))
+        rc = SPHNSE_E_NOMEM;
     if (!rc) {
         std::vector<int2> bt;
         for (int i = 0; i < n; ++i)
@@ -530,7 +619,6 @@ sphnse_ensemble* sphnse_ensemble_create(int n, const int* Ls, const double* nus,
         return nullptr;
     }
     for (auto& B : E->buckets) B.P->stream = E->stream;
-    E->ctl.resize(n);
     for (int i = 0; i < n; ++i) {
         InstPar& p = E->par[i];
         std::memset(&p, 0, sizeof(p));
@@ -569,8 +657,8 @@ static int set_precision(sphnse_ensemble* E, int prec) {
         B.tc = want;
     }
     if (E->g_rhs_alpha) cudaGraphExecDestroy(E->g_rhs_alpha);
-    if (E->g_round) cudaGraphExecDestroy(E->g_round);
-    E->g_rhs_alpha = E->g_round = nullptr;
+    if (E->g_adv) cudaGraphExecDestroy(E->g_adv);
+    E->g_rhs_alpha = E->g_adv = nullptr;
     E->precision = prec;
     return SPHNSE_OK;
 }
@@ -635,19 +723,28 @@ static int ensemble_init_inner(sphnse_ensemble* E, double t0) {
     cudaMemsetAsync(E->d_norms, 0, size_t(E->n) * 8 * sizeof(unsigned long long), E->stream);
     kb_wnorm<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, F_INIT, E->F, E->alpha, E->d_norms, 0);
     if ((rc = read_all_norms(E))) return rc;
+    std::vector<StepCtl> sc(E->n);
     for (int i = 0; i < E->n; ++i) {
         if (E->h_norms[size_t(i) * 8 + 7]) return SPHNSE_E_NONFINITE;
         const double rh = 1.25 * nrm(E, i, 0) / std::sqrt(E->rtol);
         const double h0 = rh > 0.0 ? std::min(E->h_max, 1.0 / rh) : E->h_max;
-        Ctl& c = E->ctl[i];
-        c = Ctl();
-        c.t = t0;
-        c.h = h0;
-        c.h_dif = h0;
-        c.k = 1;
+        StepCtl& S = sc[i];
+        S = StepCtl{};
+        ndf_constants(false, S.gamma, S.iga, S.ec);
+        S.nu = E->nu[i];
+        S.omega = E->Omega;
+        S.t = t0;
+        S.h = h0;
+        S.t_end = INFINITY;
+        S.h_dif = h0;
+        S.order = 1;
         E->par[i].h0 = h0;
     }
     if ((rc = upload_par(E))) return rc;
+    if (cudaMemcpyAsync(E->d_sc, sc.data(), sc.size() * sizeof(StepCtl), cudaMemcpyHostToDevice, E->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(E->stream) != cudaSuccess)
+        return SPHNSE_E_CUDA;
     kb_init<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, E->dif, E->F);
     return check_cuda(cudaGetLastError());
 }
@@ -672,233 +769,92 @@ int sphnse_ensemble_advance(sphnse_ensemble* E, int nsteps, sphnse_step_info* in
     return leave(E, ensemble_advance_inner(E, nsteps, info));
 }
 
-static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_info* info) {
-    const int n = E->n;
-    double gam[SPHNSE_MAXK], iga[SPHNSE_MAXK], ec[SPHNSE_MAXK];
-    {
-        double g = 0.0;
-        for (int k = 1; k <= SPHNSE_MAXK; ++k) {
-            g += 1.0 / k;
-            gam[k - 1] = g;
-            iga[k - 1] = 1.0 / (g * (1.0 - KAPPA_E[k - 1]));
-            ec[k - 1] = KAPPA_E[k - 1] * g + 1.0 / (k + 1.0);
+// The advance graph: open the call, set up the first round, then a WHILE node
+// over rounds (accept / rescale / predictor where flagged, one batched RHS,
+// the Newton update where flagged, the controller), then the last accepts.
+static int build_advance_graph(sphnse_ensemble* E) {
+    if (E->g_adv) return SPHNSE_OK;
+    const cudaStream_t cs = E->stream;
+    const int nctl = std::min(1024, (E->n + 31) / 32 * 32);
+    const int nblk = (E->n + CTL_THREADS - 1) / CTL_THREADS;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraph_t body = nullptr;
+    int rc = SPHNSE_OK;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+              cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+        kb_call_begin<<<1, nctl, 0, cs>>>(E->d_sc, E->d_par, E->d_norms, E->d_loop, E->n);
+        kb_round_ctl<<<nblk, CTL_THREADS, 0, cs>>>(E->d_sc, E->d_par, E->d_norms, E->d_info, E->d_loop, E->n, 0, h);
+        cudaStreamCaptureStatus status;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t node;
+        ok = cudaStreamGetCaptureInfo(cs, &status, nullptr, &capg, &deps, nullptr, &ndeps) == cudaSuccess &&
+             status == cudaStreamCaptureStatusActive;
+        if (ok) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            ok = cudaGraphAddNode(&node, capg, deps, nullptr, ndeps, &cp) == cudaSuccess &&
+                 cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                     cudaSuccess;
+            if (ok) body = cp.conditional.phGraph_out[0];
         }
+        kb_accept<<<E->nbt, EB, 0, cs>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && ok;
     }
-    const double thr = E->atol / E->rtol;
-    const int maxit = E->newton_max;
-    const size_t nb = size_t(n) * 8 * sizeof(unsigned long long);
-    int rc;
-    // one round: accept / rescale / predict where flagged, the batched RHS at
-    // ynew, the Newton update where flagged, and the norms to the host
-    rc = capture(E, &E->g_round, [&]() {
-        cudaStream_t st = E->stream;
-        if (cudaMemsetAsync(E->d_norms, 0, nb, st) != cudaSuccess) return SPHNSE_E_CUDA;
-        kb_accept<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
-        kb_rescale<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->dif);
-        kb_predict<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew,
+    ok = ok && body && cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+                           cudaSuccess;
+    if (ok) {
+        kb_accept<<<E->nbt, EB, 0, cs>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
+        kb_rescale<<<E->nbt, EB, 0, cs>>>(E->d_btab, E->d_par, E->dif);
+        kb_predict<<<E->nbt, EB, 0, cs>>>(E->d_btab, E->d_par, E->alpha, E->dif, E->y0, E->psi, E->d, E->ynew,
                                            E->d_norms);
-        int r = batched_rhs(E, E->ynew, E->F);
-        if (r) return r;
-        kb_newton<<<E->nbt, EB, 0, st>>>(E->d_btab, E->d_par, E->F, E->alpha, E->y0, E->psi, E->d, E->ynew,
-                                          E->dif, E->d_norms);
-        if (cudaMemcpyAsync(E->h_norms, E->d_norms, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            return SPHNSE_E_CUDA;
-        return check_cuda(cudaGetLastError());
-    });
-    if (rc) return rc;
-    for (int i = 0; i < n; ++i) {
-        Ctl& c = E->ctl[i];
-        c.state = nsteps > 0 ? S_START : S_IDLE;
-        c.steps_left = nsteps;
-        c.attempts = 0;
-        c.nofailed = true;
-        c.pending_accept = false;
-        c.rejections = 0;
-        c.newton = 0;
-        c.h_dif_before = c.h_dif;
+        rc = batched_rhs(E, E->ynew, E->F);
+        kb_newton<<<E->nbt, EB, 0, cs>>>(E->d_btab, E->d_par, E->F, E->alpha, E->y0, E->psi, E->d, E->ynew, E->dif,
+                                          E->d_norms);
+        kb_round_ctl<<<nblk, CTL_THREADS, 0, cs>>>(E->d_sc, E->d_par, E->d_norms, E->d_info, E->d_loop, E->n, 1, h);
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && ok && rc == SPHNSE_OK;
     }
-    E->rounds = 0;
-    for (;;) {
-        bool newton = false, accept = false;
-        for (int i = 0; i < n; ++i) {
-            Ctl& c = E->ctl[i];
-            InstPar& p = E->par[i];
-            p.flags = 0;
-            if (c.pending_accept) {
-                p.flags |= F_ACCEPT;
-                p.ka = c.acc_k;
-                c.pending_accept = false;
-                accept = true;
-            }
-            if (c.state == S_START) {
-                if (++c.attempts > 200) return SPHNSE_E_STEP_TOO_SMALL;
-                c.hmin = 16.0 * EPS * std::fabs(c.t);
-                const double h = std::min(E->h_max, std::max(c.hmin, c.h));
-                c.h = h;
-                const int k = c.k;
-                if (h != c.h_dif) {
-                    rescale_mat(k, h / c.h_dif, p.A);
-                    p.flags |= F_RESCALE;
-                    c.h_dif = h;
-                    c.nconhk = 0;
-                }
-                if (h != c.miter_h || k != c.miter_k) {
-                    c.havrate = 0;
-                    c.miter_h = h;
-                    c.miter_k = k;
-                }
-                c.ha = h;
-                c.ka = k;
-                p.k = k;
-                p.c = h * iga[k - 1];
-                p.thr = thr;
-                for (int j = 0; j < SPHNSE_MAXK; ++j) p.g[j] = j < k ? gam[j] * iga[k - 1] : 0.0;
-                p.flags |= F_PREDICT | F_NEWTON;
-                c.state = S_NEWTON;
-                c.it = 0;
-                c.its = 0;
-                c.oldnrm = 0.0;
-                c.conv = false;
-            } else if (c.state == S_NEWTON) {
-                p.flags |= F_NEWTON;
-            }
-            newton = newton || (p.flags & F_NEWTON);
-        }
-        if (!newton) {
-            // only the accepts of the last round remain
-            if (accept) {
-                if ((rc = upload_par(E))) return rc;
-                kb_accept<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, E->dif, E->d, E->alpha, E->ynew);
-                if ((rc = check_cuda(cudaGetLastError()))) return rc;
-            }
-            break;
-        }
-        if ((rc = upload_par(E))) return rc;
-        if (cudaGraphLaunch(E->g_round, E->stream) != cudaSuccess || cudaStreamSynchronize(E->stream) != cudaSuccess)
-            return SPHNSE_E_CUDA;
-        ++E->rounds;
-        for (int i = 0; i < n; ++i) {
-            Ctl& c = E->ctl[i];
-            if (!(E->par[i].flags & F_NEWTON)) continue;
-            if (E->h_norms[size_t(i) * 8 + 7]) return SPHNSE_E_NONFINITE;
-            const int it = c.it;
-            if (it == 0) c.ynorm = nrm(E, i, 4);
-            for (int q = 0; q < 4; ++q) c.nrm[q] = nrm(E, i, q);
-            c.its = it + 1;
-            // the corrector's rate test (as sphnse_step)
-            const double newnrm = c.nrm[0], minnrm = 100.0 * EPS * c.ynorm;
-            bool stop = false, conv = false;
-            if (newnrm <= minnrm) {
-                stop = conv = true;
-            } else if (it == 0) {
-                if (c.havrate) {
-                    const double errit = newnrm * c.rate / (1.0 - c.rate);
-                    if (errit <= 0.05 * E->rtol) stop = conv = true;
-                } else {
-                    c.rate = 0.0;
-                }
-            } else if (newnrm > 0.9 * c.oldnrm) {
-                stop = true;
-            } else {
-                c.rate = std::max(0.9 * c.rate, newnrm / c.oldnrm);
-                c.havrate = 1;
-                const double errit = newnrm * c.rate / (1.0 - c.rate);
-                if (errit <= 0.5 * E->rtol) stop = conv = true;
-                else if (it == maxit - 1) stop = true;
-                else if (0.5 * E->rtol < errit * std::pow(c.rate, maxit - 1 - it)) stop = true;
-            }
-            c.oldnrm = newnrm;
-            if (!stop && it + 1 < maxit) {
-                c.it = it + 1;
-                continue;
-            }
-            // the attempt is over
-            c.newton += c.its;
-            const double h = c.ha;
-            const int k = c.ka;
-            c.state = S_START;
-            if (!conv) {
-                ++c.rejections;
-                if (h <= c.hmin) return SPHNSE_E_STEP_TOO_SMALL;
-                c.h = std::max(c.hmin, 0.3 * h);
-                continue;
-            }
-            const double err = c.nrm[1] * ec[k - 1];
-            if (err > E->rtol) {
-                ++c.rejections;
-                if (h <= c.hmin) return SPHNSE_E_STEP_TOO_SMALL;
-                if (c.nofailed) {
-                    c.nofailed = false;
-                    double hopt = h * std::max(0.1, 0.833 * std::pow(E->rtol / err, 1.0 / (k + 1)));
-                    if (k > 1) {
-                        const double errkm1 = c.nrm[2] * ec[k - 2];
-                        const double hkm1 = h * std::max(0.1, 0.769 * std::pow(E->rtol / errkm1, 1.0 / k));
-                        if (hkm1 > hopt) {
-                            hopt = std::min(h, hkm1);
-                            c.k = k - 1;
-                        }
-                    }
-                    c.h = std::max(c.hmin, hopt);
-                } else {
-                    c.h = std::max(c.hmin, 0.5 * h);
-                }
-                continue;
-            }
-            // accepted: the differences are updated at the start of the next launch
-            c.pending_accept = true;
-            c.acc_k = k;
-            c.t += h;
-            c.nconhk = std::min(c.nconhk + 1, SPHNSE_MAXK + 2);
-            if (c.nconhk >= k + 2) {
-                double temp = 1.2 * std::pow(err / E->rtol, 1.0 / (k + 1));
-                double hopt = temp > 0.1 ? h / temp : 10.0 * h;
-                int kopt = k;
-                if (k > 1) {
-                    const double errkm1 = c.nrm[2] * ec[k - 2];
-                    temp = 1.3 * std::pow(errkm1 / E->rtol, 1.0 / k);
-                    const double hkm1 = temp > 0.1 ? h / temp : 10.0 * h;
-                    if (hkm1 > hopt) {
-                        hopt = hkm1;
-                        kopt = k - 1;
-                    }
-                }
-                if (k < E->max_order) {
-                    const double errkp1 = c.nrm[3] * ec[k];
-                    temp = 1.4 * std::pow(errkp1 / E->rtol, 1.0 / (k + 2));
-                    const double hkp1 = temp > 0.1 ? h / temp : 10.0 * h;
-                    if (hkp1 > hopt) {
-                        hopt = hkp1;
-                        kopt = k + 1;
-                    }
-                }
-                if (hopt > h) {
-                    c.h = hopt;
-                    if (kopt != k) {
-                        c.k = kopt;
-                        c.nconhk = 0;
-                    }
-                }
-            }
-            if (info) {
-                sphnse_step_info& o = info[i];
-                o.t = c.t;
-                o.h = h;
-                o.err = err;
-                o.order = k;
-                o.newton_iters = c.newton;
-                o.rejections = c.rejections;
-                o.rhs_evals = c.newton;
-                o.next_order = c.k;
-                o.next_h = c.h;
-                o.h_dif_before = c.h_dif_before;
-            }
-            c.nofailed = true;
-            c.attempts = 0;
-            c.h_dif_before = c.h_dif;
-            if (--c.steps_left == 0) c.state = S_IDLE;
-        }
+    if (ok) ok = cudaGraphInstantiate(&E->g_adv, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (!ok) {
+        E->g_adv = nullptr;
+        return rc ? rc : SPHNSE_E_CUDA;
     }
     return SPHNSE_OK;
+}
+
+static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_info* info) {
+    int rc;
+    if ((rc = build_advance_graph(E))) return rc;
+    EnsLoop& L = *E->h_loop;
+    L = EnsLoop{};
+    L.rtol = E->rtol;
+    L.thr = E->atol / E->rtol;
+    L.h_max = E->h_max;
+    L.nsteps = nsteps;
+    L.maxk = E->max_order;
+    L.newton_max = E->newton_max;
+    L.max_rounds = int(std::min<long>(1L << 30, long(nsteps) * 200 * (E->newton_max + 1) + 16));
+    const size_t ib = size_t(E->n) * sizeof(sphnse_step_info);
+    if (cudaMemcpyAsync(E->d_loop, E->h_loop, sizeof(EnsLoop), cudaMemcpyHostToDevice, E->stream) != cudaSuccess ||
+        cudaGraphLaunch(E->g_adv, E->stream) != cudaSuccess ||
+        cudaMemcpyAsync(E->h_loop, E->d_loop, sizeof(EnsLoop), cudaMemcpyDeviceToHost, E->stream) != cudaSuccess ||
+        (info && cudaMemcpyAsync(E->h_info, E->d_info, ib, cudaMemcpyDeviceToHost, E->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(E->stream) != cudaSuccess)
+        return SPHNSE_E_CUDA;
+    E->rounds = L.rounds;
+    if (info && nsteps > 0) std::memcpy(info, E->h_info, ib);
+    return L.status;
 }
 
 }  // extern "C"

@@ -136,6 +136,9 @@ struct StepCtl {
     int status;                              // SPHNSE_OK, else the error that ended the loop
     int k, do_rescale;                       // the current attempt
     int accept, k_acc;                       // the last attempt was accepted at order k_acc
+    double err;                              // its error estimate
+    int sum_newton, sum_rejections;          // over the accepted steps of the call
+    int phase;                               // ensemble rounds: 0 idle, 1 new attempt next, 2 in Newton
     double h_att;
     double A[SPHNSE_MAXK * SPHNSE_MAXK];     // difference rescaling matrix (do_rescale)
     double g[SPHNSE_MAXK];                   // predictor weights of psi
