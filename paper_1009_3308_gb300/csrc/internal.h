@@ -114,7 +114,8 @@ struct TcBatchA {
 // results updated by the loop's control kernel.
 struct NewtonCtl {
     double c, nu, omega, thr, rtol, rate;   // inputs (rate: the running contraction estimate)
-    int k, maxit, tight, fp64, havrate, pad0;
+    int k, maxit, tight, fp64, havrate;
+    unsigned arrived;                       // blocks of the Newton update done with this iteration
     double nrm[4], ynorm, oldnrm;           // results / loop state
     int it, its, conv, stop, nonfinite, pad1;
 };

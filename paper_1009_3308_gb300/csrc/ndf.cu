@@ -155,11 +155,14 @@ __global__ void k_newton(const double2* F, const double2* y, const double2* y0, 
     block_amax_f<4>(slot, nv, id, bad);
 }
 
-// The same update with its parameters read from the device-side loop state
-// (a graph node keeps fixed arguments; c, k and the weights change per attempt)
+// The same update inside the graphs' Newton loop: parameters read from the
+// device-side loop state (a graph node keeps fixed arguments; c, k and the
+// weights change per attempt), and the last block to finish applies the
+// stopping rule to the iteration's norms, clears the slots the next
+// iteration fills and sets the WHILE condition (0: stop).
 __global__ void k_newton_g(const double2* F, const double2* y, const double2* y0, const double2* psi, double2* d,
-                           double2* ynew, const double2* dif, const int2* lm, const NewtonCtl* ctl,
-                           unsigned long long* slot, int n) {
+                           double2* ynew, const double2* dif, const int2* lm, NewtonCtl* ctl,
+                           unsigned long long* slot, int n, cudaGraphConditionalHandle h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = ctl->k;
     float nv[4] = {0.f, 0.f, 0.f, 0.f};
@@ -176,17 +179,16 @@ __global__ void k_newton_g(const double2* F, const double2* y, const double2* y0
     }
     const int id[4] = {0, 1, 2, 3};
     block_amax_f<4>(slot, nv, id, bad);
-}
-
-// One thread: the corrector's stopping rule after iteration ctl->it, then
-// clear the slots the next iteration fills and set the WHILE condition (0: stop).
-__global__ void k_newton_ctl(NewtonCtl* ctl, unsigned long long* slots, cudaGraphConditionalHandle h) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double nv[5];
-    for (int q = 0; q < 5; ++q) nv[q] = __longlong_as_double(static_cast<long long>(slots[q]));
-    const bool stop = newton_control(*ctl, nv, slots[7] != 0ull);
-    for (int q = 0; q < 4; ++q) slots[q] = 0ull;
-    slots[7] = 0ull;
+    __threadfence();   // this block's slot updates before its arrival
+    __syncthreads();
+    if (threadIdx.x != 0 || atomicAdd(&ctl->arrived, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    double v[5];
+    for (int q = 0; q < 5; ++q) v[q] = __longlong_as_double(static_cast<long long>(__ldcg(slot + q)));
+    const bool stop = newton_control(*ctl, v, __ldcg(slot + 7) != 0ull);
+    for (int q = 0; q < 4; ++q) slot[q] = 0ull;
+    slot[7] = 0ull;
+    ctl->arrived = 0u;
     cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
@@ -513,8 +515,8 @@ int rescale(sphnse_plan* P, sphnse_state* st, double h, int k) {
 }
 
 // The corrector's Newton loop as one graph launch: a WHILE node whose body is
-// the RHS at ynew, the Newton update and the control kernel, which sets the
-// loop condition on the device, so an attempt costs one host round trip
+// the RHS at ynew and the Newton update, whose last block sets the loop
+// condition on the device, so an attempt costs one host round trip
 // instead of one per iteration.  Built per (state, forcing, precision, nu,
 // Omega) after the plan's kernels are set up; any failure to capture leaves
 // the host loop in charge.
@@ -564,8 +566,7 @@ bool newton_graph_ready(sphnse_plan* P, sphnse_state* st, const double* forcing)
                                       reinterpret_cast<double*>(W.F));
             k_newton_g<<<grid(n), 256, 0, P->cap_stream>>>(
                 W.F, reinterpret_cast<const double2*>(st->alpha), W.y0, W.psi, W.d, W.ynew,
-                reinterpret_cast<const double2*>(st->dif), P->d_lm, P->d_ctl, P->d_norms, n);
-            k_newton_ctl<<<1, 32, 0, P->cap_stream>>>(P->d_ctl, P->d_norms, h);
+                reinterpret_cast<const double2*>(st->dif), P->d_lm, P->d_ctl, P->d_norms, n, h);
             cudaGraph_t out = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &out);
             ok = rc == SPHNSE_OK && ce == cudaSuccess;
@@ -792,8 +793,7 @@ bool step_graph_ready(sphnse_plan* P, sphnse_state* st, const double* forcing) {
     if (ok) {
         const int rc = rhs_device(P, reinterpret_cast<const double*>(W.ynew), forcing, reinterpret_cast<double*>(W.F));
         k_newton_g<<<grid(n), 256, 0, cs>>>(W.F, alpha, W.y0, W.psi, W.d, W.ynew, dif, P->d_lm, &P->d_step->nc,
-                                            P->d_norms, n);
-        k_newton_ctl<<<1, 32, 0, cs>>>(&P->d_step->nc, P->d_norms, hnewton);
+                                            P->d_norms, n, hnewton);
         ok = end() && rc == SPHNSE_OK;
     }
     P->stream = saved;
