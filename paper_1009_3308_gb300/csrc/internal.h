@@ -108,10 +108,10 @@ struct TcBatchA {
     unsigned char* stiles = nullptr;   // [instance][block][kt] 1 KB
 };
 
-// tcgen05 path state (tensor maps and item schedules, built on first use)
-// Device-side simplified-Newton loop of one corrector (a CUDA graph with a
-// conditional WHILE node): inputs written by the host per attempt, state and
-// results updated by the loop's control kernel.
+// Simplified-Newton loop state of one corrector attempt: inputs set when the
+// attempt starts (by the host or the step loop's controller), loop state and
+// results updated after every iteration by the stopping rule (on the host, or
+// in the last block of the graph's Newton update).
 struct NewtonCtl {
     double c, nu, omega, thr, rtol, rate;   // inputs (rate: the running contraction estimate)
     int k, maxit, tight, fp64, havrate;
@@ -157,6 +157,7 @@ struct HostIO {
     bool ready = false;
 };
 
+// tcgen05 path state (tensor maps and item schedules, built on first use)
 struct TcState {
     void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
     void* map_lo = nullptr;
