@@ -339,7 +339,8 @@ int sphnse_ensemble_step(sphnse_ensemble* ens, sphnse_step_info* info);
  * rejected attempts or Newton iterations and the host waits once per call.  Each instance follows exactly the
  * step/order sequence sphnse_step gives it alone.  info (host, n entries or
  * NULL): the last step's t, h, err, order, next_order, next_h, h_dif_before,
- * with newton_iters, rhs_evals and rejections summed over the call. */
+ * with newton_iters, rhs_evals and rejections summed over the call.
+ * SPHNSE_E_ARG before sphnse_ensemble_init. */
 int sphnse_ensemble_advance(sphnse_ensemble* ens, int nsteps, sphnse_step_info* info);
 
 /* ---- stage timing ------------------------------------------------------- */

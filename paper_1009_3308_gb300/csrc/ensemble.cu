@@ -349,7 +349,8 @@ struct sphnse_ensemble {
     sphnse_step_info* h_info = nullptr;  // pinned
     cudaGraphExec_t g_rhs_alpha = nullptr, g_adv = nullptr;
     int max_n = 0;
-    long rounds = 0;                 // graph launches of the last advance
+    long rounds = 0;                 // rounds of the last advance
+    bool inited = false;             // sphnse_ensemble_init has set the controllers up
 };
 
 namespace {
@@ -745,6 +746,7 @@ static int ensemble_init_inner(sphnse_ensemble* E, double t0) {
             cudaSuccess ||
         cudaStreamSynchronize(E->stream) != cudaSuccess)
         return SPHNSE_E_CUDA;
+    E->inited = true;
     kb_init<<<E->nbt, EB, 0, E->stream>>>(E->d_btab, E->d_par, E->dif, E->F);
     return check_cuda(cudaGetLastError());
 }
@@ -834,6 +836,7 @@ static int build_advance_graph(sphnse_ensemble* E) {
 }
 
 static int ensemble_advance_inner(sphnse_ensemble* E, int nsteps, sphnse_step_info* info) {
+    if (!E->inited) return SPHNSE_E_ARG;
     int rc;
     if ((rc = build_advance_graph(E))) return rc;
     EnsLoop& L = *E->h_loop;

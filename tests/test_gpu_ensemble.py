@@ -128,3 +128,13 @@ def test_full_ensemble_rhs_matches_oracle_on_sampled_members(precision, tol):
         assert err <= tol, (i, m["L"], err)
     for i in range(len(mem)):
         assert torch.isfinite(torch.view_as_real(ens.get(i, "F"))).all(), i
+
+
+def test_advance_before_init_is_an_argument_error():
+    from paper_1009_3308_gb300 import Ensemble, SphnseError
+    ens = Ensemble([31, 31], [1e-3, 1e-3], 1.0)
+    with pytest.raises(SphnseError, match="E_ARG"):
+        ens.advance(1)
+    ens.set_alpha(0, _dev(coefficients(31, 7, 0.1)))
+    ens.init(0.0)
+    assert len(ens.advance(0)) == 2
