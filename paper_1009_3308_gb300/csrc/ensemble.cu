@@ -466,11 +466,14 @@ int leave(sphnse_ensemble* E, int rc) {
 }
 
 int smallest_grid(int L) {
-    // smallest even M = 2^a 3^b >= 3L + 2
+    // smallest M = 2^a 3^b >= 3L + 2 (exact quadrature, Eq. (M_choice)) that
+    // the batched FP32 streaming kernels take: M >= 128 and a multiple of 16,
+    // i.e. nh = M / 4 northern latitudes, at least 32 and a multiple of 4.
+    // A grid above 3L + 2 gives the same F (up to rounding).
     int best = 0;
     for (long a = 2; a <= 4096; a *= 2)
         for (long m = a; m <= 4096; m *= 3)
-            if (m >= 3 * L + 2 && m % 2 == 0 && (best == 0 || m < best)) best = int(m);
+            if (m >= 3 * L + 2 && m >= 128 && m % 16 == 0 && (best == 0 || m < best)) best = int(m);
     return best;
 }
 

@@ -138,3 +138,26 @@ def test_advance_before_init_is_an_argument_error():
     ens.set_alpha(0, _dev(coefficients(31, 7, 0.1)))
     ens.init(0.0)
     assert len(ens.advance(0)) == 2
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_small_and_uneven_truncations_match_oracle(precision):
+    """Truncations whose own smallest grid the batched kernels do not take
+    (L = 1, 5, 31: fewer than 32 northern latitudes; L = 50: 3L + 2 = 152)
+    run on a larger exact grid; F is the same (Eq. (M_choice))."""
+    from oracle.rhs import Problem, rhs_separable
+    from paper_1009_3308_gb300 import Ensemble
+    Ls, nus = [31, 50, 5, 31, 1], [1e-3, 2e-4, 1e-2, 5e-4, 1e-2]
+    ens = Ensemble(Ls, nus, 1.0, precision=precision)
+    alphas = [coefficients(L, 300 + i, 0.1) * 3 for i, L in enumerate(Ls)]
+    for i, a in enumerate(alphas):
+        ens.set_alpha(i, _dev(a))
+    ens.rhs()
+    for i, (L, nu) in enumerate(zip(Ls, nus)):
+        M = 3 * (L + 1) + (3 * (L + 1)) % 2
+        ref = rhs_separable(Problem(L, M, nu, 1.0), alphas[i])
+        got = ens.get(i, "F").cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 3e-5 * np.linalg.norm(ref), (i, L)
+    ens.init(0.0)
+    infos = ens.advance(3)
+    assert all(x["t"] > 0.0 for x in infos)
