@@ -112,6 +112,19 @@ def test_enstrophy_invariant_needs_exact_quadrature():
     assert abs(z) > 1e-4
 
 
+@pytest.mark.parametrize("N,M1,M2", [(12, 38, 48), (31, 96, 128), (5, 18, 64)])
+def test_rhs_is_the_same_on_every_exact_grid(N, M1, M2):
+    """Any even M >= 3N + 2 integrates the Galerkin terms exactly (Eq.
+    (M_choice)), so F does not depend on the grid beyond rounding; below the
+    bound it does."""
+    a = random_packed(N, 21)
+    F1 = rhs_separable(Problem(N, M1, 1e-3, 1.0), a)
+    F2 = rhs_separable(Problem(N, M2, 1e-3, 1.0), a)
+    assert np.linalg.norm(F1 - F2) <= 1e-13 * np.linalg.norm(F1)
+    F0 = rhs_separable(Problem(N, 2 * N + 2, 1e-3, 1.0), a)
+    assert np.linalg.norm(F0 - F1) > 1e-6 * np.linalg.norm(F1)
+
+
 @pytest.mark.parametrize("L", [1, 4, 9])
 def test_single_degree_rossby_haurwitz(L):
     """All coefficients on one degree: B(u,u) is a gradient, so only the
