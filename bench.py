@@ -481,7 +481,8 @@ def extra_ensemble(torch, nsteps=200, n=256, precision="fp32"):
             "mean_rhs_per_instance_step": rhs / (n * nsteps),
             "instances": n, "steps": nsteps, "seconds": el,
             "stepping": "asynchronous rounds (sphnse_ensemble_advance)",
-            "buckets": sorted(set(m["L"] for m in mem)), "precision": precision}
+            "buckets": sorted(set(m["L"] for m in mem)), "precision": precision,
+            "synthesis_shapes": ens.buckets() if precision == "bf16x3" else None}
 
 
 def cpu_baseline(w, target_s=15.0):

@@ -72,6 +72,10 @@ extern "C" {
                                          adjoint always carries it in the product) */
 #define SPHNSE_KEY_TIMING_PERIOD  11  /* stage timing records every period-th launch of a
                                          timed stage (default 1) */
+#define SPHNSE_KEY_AUTOTUNE       12  /* ensemble: 1 (default) times the candidate shapes of
+                                        * the tensor-core synthesis per truncation when BF16X3
+                                        * is selected and keeps the fastest (sphnse_ensemble_bucket);
+                                        * 0 takes the widest instance groups; set it first */
 #define SPHNSE_KEY_N_COEFF       100  /* read-only: n_coeff */
 #define SPHNSE_KEY_L             101  /* read-only: truncation degree */
 #define SPHNSE_KEY_NLAT          102  /* read-only */
@@ -83,6 +87,7 @@ extern "C" {
                                          synthesis reads (tiles of negligible entries
                                          excluded; 0 before the BF16X3 tables exist) */
 #define SPHNSE_KEY_ANA_ENTRIES   107  /* read-only: the same for the tensor-core analysis */
+#define SPHNSE_KEY_BUCKETS       108  /* read-only (ensemble): truncation buckets */
 
 #define SPHNSE_FP64    0  /* FP64 tables and arithmetic throughout */
 #define SPHNSE_FP32    1  /* FP32 tables, contractions, FFTs; FP64 state and update */
@@ -318,6 +323,15 @@ int sphnse_ensemble_set_stream(sphnse_ensemble* ens, void* stream);
 /* Device pointers (owned by the ensemble) of instance i's packed state alpha
  * and of its last RHS F (complex128, n_coeff entries); any output may be NULL. */
 int sphnse_ensemble_instance(sphnse_ensemble* ens, int i, double** alpha, double** F, int* n_coeff);
+
+/* Bucket b (0 .. SPHNSE_KEY_BUCKETS - 1; instances of one truncation share its
+ * Legendre tables): its truncation L, instance count, and on the BF16X3
+ * tensor-core path the shape of its synthesis (instances per group, pipeline
+ * stages) and that synthesis' duration in microseconds as timed by the
+ * autotuner (0 when not tuned; group = stages = 0 off the tensor-core path).
+ * Any output may be NULL. */
+int sphnse_ensemble_bucket(sphnse_ensemble* ens, int b, int* L, int* count, int* group, int* stages,
+                           double* syn_us);
 
 /* F_i = F(alpha_i) for every instance (Eq. (ode)), as one CUDA-graph launch. */
 int sphnse_ensemble_rhs(sphnse_ensemble* ens);

@@ -311,6 +311,7 @@ struct Bucket {
     TcBatch tcb;               // BF16X3: instance groups of the tensor-core synthesis
     TcBatchA tca;              //         and slots of the tensor-core analysis
     bool tc = false;
+    double syn_us = 0;         // tuned synthesis duration (0: not tuned)
 };
 
 }  // namespace
@@ -351,6 +352,7 @@ struct sphnse_ensemble {
     int max_n = 0;
     long rounds = 0;                 // rounds of the last advance
     bool inited = false;             // sphnse_ensemble_init has set the controllers up
+    bool autotune = true;            // time the tensor-core synthesis shapes per bucket
 };
 
 namespace {
@@ -646,6 +648,61 @@ int sphnse_ensemble_set_stream(sphnse_ensemble* E, void* stream) {
 // BF16X3: the buckets whose grids the tensor-core kernels support get their
 // BF16 hi/lo tables, tensor maps and instance groups now (none of it may be
 // allocated while a graph is being captured); the captured graphs are rebuilt.
+// Autotuner of the batched tensor-core synthesis of one bucket: every
+// (instances per group, pipeline stages) shape that fits (group widths 1..9,
+// stages 6, 5, 4) is built, its B tiles prepared from the current states and
+// its synthesis timed with CUDA events (one warm-up, three timed launches on
+// the ensemble's stream); the fastest is kept.  The shape changes neither the
+// result of an instance's column nor the other stages.
+static int tune_synthesis(sphnse_ensemble* E, Bucket& B) {
+    sphnse_plan* P = B.P;
+    const double* xb = reinterpret_cast<const double*>(E->alpha + B.off);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return SPHNSE_E_CUDA;
+    }
+    TcBatch best;
+    float best_ms = 0.f;
+    std::vector<std::pair<int, int>> seen;
+    int rc = SPHNSE_OK;
+    for (int ng = 1; ng <= std::min(B.nb, 9) && !rc; ++ng)
+        for (int ns = 6; ns >= 4 && !rc; --ns) {
+            TcBatch T;
+            if ((rc = tc_batch_init(P, B.nb, &T, ng, ns))) break;
+            const std::pair<int, int> shape(T.ng, T.ns);
+            if (T.ns < 4 || std::find(seen.begin(), seen.end(), shape) != seen.end()) {
+                tc_batch_free(&T);
+                continue;
+            }
+            seen.push_back(shape);
+            float ms = 0.f;
+            rc = launch_prep_tc_batch(P, T, xb);
+            if (!rc) rc = launch_synthesis_tc_batch(P, T, B.gsyn, B.sg, 0);
+            if (!rc && cudaEventRecord(e0, E->stream) != cudaSuccess) rc = SPHNSE_E_CUDA;
+            for (int r = 0; r < 3 && !rc; ++r) rc = launch_synthesis_tc_batch(P, T, B.gsyn, B.sg, 0);
+            if (!rc && (cudaEventRecord(e1, E->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = SPHNSE_E_CUDA;
+            if (!rc && (!best.btiles || ms < best_ms)) {
+                tc_batch_free(&best);
+                best = T;
+                best_ms = ms;
+            } else {
+                tc_batch_free(&T);
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || !best.btiles) {
+        tc_batch_free(&best);
+        return rc ? rc : SPHNSE_E_UNSUPPORTED;
+    }
+    B.tcb = best;
+    B.syn_us = 1e3 * best_ms / 3.0;
+    return SPHNSE_OK;
+}
+
 static int set_precision(sphnse_ensemble* E, int prec) {
     if (prec != SPHNSE_FP32 && prec != SPHNSE_BF16X3) return SPHNSE_E_UNSUPPORTED;
     if (E->stream) cudaStreamSynchronize(E->stream);
@@ -654,7 +711,7 @@ static int set_precision(sphnse_ensemble* E, int prec) {
         if (want && !B.tcb.btiles) {
             int rc = ensure_tables(B.P, SPHNSE_BF16X3);
             if (!rc) rc = tc_setup_synthesis(B.P);
-            if (!rc) rc = tc_batch_init(B.P, B.nb, &B.tcb);
+            if (!rc) rc = E->autotune ? tune_synthesis(E, B) : tc_batch_init(B.P, B.nb, &B.tcb);
             if (!rc) rc = tc_batch_ana_init(B.P, B.nb, &B.tca);
             if (rc) return rc;
         }
@@ -676,6 +733,7 @@ int sphnse_ensemble_set(sphnse_ensemble* E, int key, double v) {
         case SPHNSE_KEY_NEWTON_MAX_ITER: if (v < 1 || v > 1000) return SPHNSE_E_ARG; E->newton_max = int(v); return SPHNSE_OK;
         case SPHNSE_KEY_H_MAX: if (v <= 0) return SPHNSE_E_ARG; E->h_max = v; return SPHNSE_OK;
         case SPHNSE_KEY_PRECISION: return set_precision(E, int(v));
+        case SPHNSE_KEY_AUTOTUNE: if (v != 0 && v != 1) return SPHNSE_E_ARG; E->autotune = v != 0; return SPHNSE_OK;
         default: return SPHNSE_E_ARG;
     }
 }
@@ -690,6 +748,8 @@ int sphnse_ensemble_get(sphnse_ensemble* E, int key, double* v) {
         case SPHNSE_KEY_H_MAX: *v = E->h_max; break;
         case SPHNSE_KEY_PRECISION: *v = E->precision; break;
         case SPHNSE_KEY_ROUNDS: *v = double(E->rounds); break;
+        case SPHNSE_KEY_AUTOTUNE: *v = E->autotune ? 1.0 : 0.0; break;
+        case SPHNSE_KEY_BUCKETS: *v = double(E->buckets.size()); break;
         default: return SPHNSE_E_ARG;
     }
     return SPHNSE_OK;
@@ -700,6 +760,18 @@ int sphnse_ensemble_instance(sphnse_ensemble* E, int i, double** alpha, double**
     if (alpha) *alpha = reinterpret_cast<double*>(E->alpha + E->off[i]);
     if (F) *F = reinterpret_cast<double*>(E->F + E->off[i]);
     if (n_coeff) *n_coeff = E->nco[i];
+    return SPHNSE_OK;
+}
+
+int sphnse_ensemble_bucket(sphnse_ensemble* E, int b, int* L, int* count, int* group, int* stages,
+                           double* syn_us) {
+    if (!E || b < 0 || b >= int(E->buckets.size())) return SPHNSE_E_ARG;
+    const Bucket& B = E->buckets[size_t(b)];
+    if (L) *L = B.L;
+    if (count) *count = B.nb;
+    if (group) *group = B.tc ? B.tcb.ng : 0;
+    if (stages) *stages = B.tc ? B.tcb.ns : 0;
+    if (syn_us) *syn_us = B.tc ? B.syn_us : 0.0;
     return SPHNSE_OK;
 }
 

@@ -301,7 +301,9 @@ int launch_synthesis_tc(sphnse_plan* P, int pairs);
 int launch_prep_tc(sphnse_plan* P, const double* alpha);
 // batched tcgen05 synthesis over nb instances of P's truncation (ensembles)
 int tc_setup_synthesis(sphnse_plan* P);
-int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B);
+// instance groups of at most ngmax (<= 9) instances, at most nsmax (<= 6)
+// pipeline stages (fewer when the shared memory does not hold them)
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax = 9, int nsmax = 6);
 void tc_batch_free(TcBatch* B);
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha);
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs);

@@ -1159,19 +1159,19 @@ int tc_setup_synthesis(sphnse_plan* P) {
 // instances share every A tile (MMA N = brows = 14 ng rounded up to 16),
 // B tiles [group][tile][brows][64], items (m, latitude tile, group) in LPT
 // order over one CTA per SM.
-int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B) {
-    if (nb < 1) return SPHNSE_E_ARG;
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax) {
+    if (nb < 1 || ngmax < 1 || nsmax < 1) return SPHNSE_E_ARG;
     const int N = P->N, nh = P->nh;
     TcBatch T;
     T.nb = nb;
     // 14 B rows per instance (12 coefficient rows, 2 for u_phi at m = 0); two
     // accumulators of brows <= 128 columns per buffer fit TMEM's 512
-    T.ng = std::min(nb, 9);
+    T.ng = std::min(nb, std::min(ngmax, 9));
     T.ngroups = (nb + T.ng - 1) / T.ng;
     T.ng = (nb + T.ngroups - 1) / T.ngroups;   // balanced groups
     T.brows = ((14 * T.ng + 15) / 16) * 16;
     const size_t stage = 2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2;
-    T.ns = int(std::min<size_t>(6, (size_t(227) * 1024 - 1024 - 512) / stage));
+    T.ns = int(std::min<size_t>(std::min(nsmax, 6), (size_t(227) * 1024 - 1024 - 512) / stage));
     const size_t bytes = size_t(T.ngroups) * P->tc.ntiles * T.brows * TC_TILE_K * 2;
     if (cudaMalloc(reinterpret_cast<void**>(&T.btiles), bytes) != cudaSuccess) return SPHNSE_E_NOMEM;
     cudaMemset(T.btiles, 0, bytes);

@@ -161,3 +161,28 @@ def test_small_and_uneven_truncations_match_oracle(precision):
     ens.init(0.0)
     infos = ens.advance(3)
     assert all(x["t"] > 0.0 for x in infos)
+
+
+def test_autotuned_synthesis_shape_gives_the_same_rhs():
+    """The autotuner picks, per truncation, the instance-group width and
+    pipeline depth of the tensor-core synthesis by timing; the shape does not
+    change any instance's result."""
+    from paper_1009_3308_gb300 import Ensemble
+    Ls = [63] * 12 + [127] * 3
+    nus = [1e-4 * (1 + i) for i in range(len(Ls))]
+    alphas = [coefficients(L, 700 + i, 0.05) * 3 for i, L in enumerate(Ls)]
+    out = {}
+    for tune in (True, False):
+        ens = Ensemble(Ls, nus, 1.0, precision="bf16x3", autotune=tune)
+        for i, a in enumerate(alphas):
+            ens.set_alpha(i, _dev(a))
+        ens.rhs()
+        out[tune] = ([ens.get(i, "F").cpu().numpy() for i in range(len(Ls))], ens.buckets())
+    for got, ref in zip(out[True][0], out[False][0]):
+        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    tuned, fixed = out[True][1], out[False][1]
+    assert [b["L"] for b in tuned] == [63, 127] and [b["instances"] for b in tuned] == [12, 3]
+    for b in tuned:
+        assert 1 <= b["group"] <= 9 and 4 <= b["stages"] <= 6 and b["syn_us"] > 0.0, b
+    assert [b["group"] for b in fixed] == [6, 3] and all(b["syn_us"] == 0.0 for b in fixed)
+    print(tuned)
