@@ -1,9 +1,9 @@
 // The NDF step controller (Sec. 4.2): constants of the scheme, the
 // difference rescaling matrix, the simplified-Newton stopping rule and the
 // attempt start / finish with step rejection and order / step selection.
-// Host-and-device functions on a StepCtl, so that the single-plan step loop
-// (one thread of a graph-launched kernel, or the host), and the ensemble's
-// per-instance rounds run the same decisions.
+// Host-and-device functions on a StepCtl: the single-plan step loop (one
+// thread of a graph-launched kernel, or the host) and the ensemble's
+// per-instance rounds take their decisions with the same code.
 #pragma once
 #include <cmath>
 
