@@ -34,6 +34,7 @@
 #include "internal.h"
 #include "controller.cuh"
 #include "dmath.cuh"
+#include "ndf_entry.cuh"
 #include "newton.cuh"
 #include "reduce.cuh"
 
@@ -100,43 +101,17 @@ __global__ void kb_init(const int2* btab, const InstPar* par, double2* dif, cons
 
 __global__ void kb_rescale(const int2* btab, const InstPar* par, double2* dif) {
     INST_PROLOGUE(F_RESCALE)
-    double2* D = dif + 7 * o;
-    double2 old[SPHNSE_MAXK];
-    for (int j = 0; j < p.k; ++j) old[j] = D[size_t(j) * p.n + i];
-    for (int j = 0; j < p.k; ++j) {
-        double sx = 0.0, sy = 0.0;
-        for (int l = 0; l < p.k; ++l) {
-            const double a = p.A[l * SPHNSE_MAXK + j];
-            sx += a * old[l].x;
-            sy += a * old[l].y;
-        }
-        D[size_t(j) * p.n + i] = make_double2(sx, sy);
-    }
+    rescale_entry(dif + 7 * o, p.A, p.k, p.n, i);
 }
 
 __global__ void kb_predict(const int2* btab, const InstPar* par, const double2* y, const double2* dif, double2* y0,
                            double2* psi, double2* d, double2* ynew, unsigned long long* norms) {
     INST_PROLOGUE_ALL(F_PREDICT)
     float r[1] = {0.f};
-    if (i < p.n) {
-        const double2* D = dif + 7 * o;
-        const double2 yi = y[o + i];
-        double2 a = yi, q = make_double2(0.0, 0.0);
-        for (int j = 0; j < p.k; ++j) {
-            const double2 dj = D[size_t(j) * p.n + i];
-            a.x += dj.x;
-            a.y += dj.y;
-            q.x += p.g[j] * dj.x;
-            q.y += p.g[j] * dj.y;
-        }
-        y0[o + i] = a;
-        ynew[o + i] = a;
-        psi[o + i] = q;
-        d[o + i] = make_double2(0.0, 0.0);
-        // slot 4: ||y / max(|y|, thr)||_inf (FP32, as the corrector's norms)
-        const float thr = fmaxf(float(p.thr), 1e-30f), ax = absf_trunc(yi.x), ay = absf_trunc(yi.y);
-        r[0] = fmaxf(ax / fmaxf(ax, thr), ay / fmaxf(ay, thr));
-    }
+    // slot 4: ||y / max(|y|, thr)||_inf (FP32, as the corrector's norms)
+    if (i < p.n)
+        r[0] = predict_entry(y + o, dif + 7 * o, p.g, p.k, y0 + o, psi + o, d + o, ynew + o,
+                             fmaxf(float(p.thr), 1e-30f), p.n, i);
     const int id[1] = {4};
     block_amax_f<1>(norms + 8 * bt.x, r, id, false);
 }
@@ -166,20 +141,7 @@ __global__ void kb_newton(const int2* btab, const InstPar* par, const double2* F
 __global__ void kb_accept(const int2* btab, const InstPar* par, double2* dif, const double2* d, double2* y,
                           const double2* ynew) {
     INST_PROLOGUE(F_ACCEPT)
-    double2* D = dif + 7 * o;
-    const int k = p.ka;
-    const double2 dd = d[o + i], dk = D[size_t(k) * p.n + i];
-    D[size_t(k + 1) * p.n + i] = make_double2(dd.x - dk.x, dd.y - dk.y);
-    double2 up = dd;
-    D[size_t(k) * p.n + i] = dd;
-    for (int j = k - 1; j >= 0; --j) {
-        double2 v = D[size_t(j) * p.n + i];
-        v.x += up.x;
-        v.y += up.y;
-        D[size_t(j) * p.n + i] = v;
-        up = v;
-    }
-    y[o + i] = ynew[o + i];
+    accept_entry(dif + 7 * o, d + o, y + o, ynew + o, p.ka, p.n, i);
 }
 
 // Per-call inputs and results of the device round loop.

@@ -26,6 +26,7 @@
 #include "internal.h"
 #include "controller.cuh"
 #include "dmath.cuh"
+#include "ndf_entry.cuh"
 #include "newton.cuh"
 #include "reduce.cuh"
 
@@ -79,20 +80,6 @@ __global__ void k_wnorm(const double2* v, const double2* y, double thr, unsigned
     block_amax<1>(slots, r, id);
 }
 
-__device__ __forceinline__ void rescale_entry(double2* dif, const double* A, int k, int n, int i) {
-    double2 old[SPHNSE_MAXK];
-    for (int j = 0; j < k; ++j) old[j] = dif[size_t(j) * n + i];
-    for (int j = 0; j < k; ++j) {
-        double sx = 0.0, sy = 0.0;
-        for (int l = 0; l < k; ++l) {
-            const double a = A[l * SPHNSE_MAXK + j];
-            sx += a * old[l].x;
-            sy += a * old[l].y;
-        }
-        dif[size_t(j) * n + i] = make_double2(sx, sy);
-    }
-}
-
 __global__ void k_rescale(double2* dif, Mat A, int k, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) rescale_entry(dif, A.a, k, n, i);
@@ -106,23 +93,7 @@ __device__ __forceinline__ void predict_block(const double2* y, const double2* d
                                               unsigned long long* slots, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float r[1] = {0.f};
-    if (i < n) {
-        const double2 yi = y[i];
-        double2 a = yi, p = make_double2(0.0, 0.0);
-        for (int j = 0; j < k; ++j) {
-            const double2 dj = dif[size_t(j) * n + i];
-            a.x += dj.x;
-            a.y += dj.y;
-            p.x += g[j] * dj.x;
-            p.y += g[j] * dj.y;
-        }
-        y0[i] = a;
-        ynew[i] = a;
-        psi[i] = p;
-        d[i] = make_double2(0.0, 0.0);
-        const float ax = absf_trunc(yi.x), ay = absf_trunc(yi.y);
-        r[0] = fmaxf(ax / fmaxf(ax, thr), ay / fmaxf(ay, thr));
-    }
+    if (i < n) r[0] = predict_entry(y, dif, g, k, y0, psi, d, ynew, thr, n, i);
     const int id[1] = {4};
     block_amax_f<1>(slots, r, id, false);
 }
@@ -193,22 +164,6 @@ __global__ void k_newton_g(const double2* F, const double2* y, const double2* y0
 }
 
 // D_{k+1} = d - D_k; D_k = d; D_j += D_{j+1} (j = k-1..0); y = ynew
-__device__ __forceinline__ void accept_entry(double2* dif, const double2* d, double2* y, const double2* ynew, int k,
-                                             int n, int i) {
-    const double2 dd = d[i], dk = dif[size_t(k) * n + i];
-    dif[size_t(k + 1) * n + i] = make_double2(dd.x - dk.x, dd.y - dk.y);
-    double2 up = dd;
-    dif[size_t(k) * n + i] = dd;
-    for (int j = k - 1; j >= 0; --j) {
-        double2 v = dif[size_t(j) * n + i];
-        v.x += up.x;
-        v.y += up.y;
-        dif[size_t(j) * n + i] = v;
-        up = v;
-    }
-    y[i] = ynew[i];
-}
-
 __global__ void k_accept(double2* dif, const double2* d, double2* y, const double2* ynew, int k, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) accept_entry(dif, d, y, ynew, k, n, i);
