@@ -83,20 +83,14 @@ __global__ void kb_wnorm(const int2* btab, const InstPar* par, int flag, const d
                          unsigned long long* norms, int slot) {
     INST_PROLOGUE_ALL(flag)
     double r[1] = {0.0};
-    if (i < p.n) {
-        const double2 a = v[o + i], b = y[o + i];
-        r[0] = fmax(fabs(a.x) * rcp64<1>(fmax(fabs(b.x), p.thr)), fabs(a.y) * rcp64<1>(fmax(fabs(b.y), p.thr)));
-    }
+    if (i < p.n) r[0] = wnorm_entry(v[o + i], y[o + i], p.thr);
     const int id[1] = {slot};
     block_amax<1>(norms + 8 * bt.x, r, id);
 }
 
 __global__ void kb_init(const int2* btab, const InstPar* par, double2* dif, const double2* F) {
     INST_PROLOGUE(F_INIT)
-    const double2 f = F[o + i];
-    double2* D = dif + 7 * o;
-    D[i] = make_double2(p.h0 * f.x, p.h0 * f.y);
-    for (int j = 1; j < SPHNSE_MAXK + 2; ++j) D[size_t(j) * p.n + i] = make_double2(0.0, 0.0);
+    init_dif_entry(dif + 7 * o, F + o, p.h0, p.n, i);
 }
 
 __global__ void kb_rescale(const int2* btab, const InstPar* par, double2* dif) {

@@ -62,20 +62,14 @@ inline double d2u_max(unsigned long long v) {
 
 __global__ void k_zero_dif(double2* dif, const double2* F, double h, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double2 f = F[i];
-    dif[i] = make_double2(h * f.x, h * f.y);
-    for (int j = 1; j < SPHNSE_MAXK + 2; ++j) dif[size_t(j) * n + i] = make_double2(0.0, 0.0);
+    if (i < n) init_dif_entry(dif, F, h, n, i);
 }
 
 // ||v / max(|y|, thr)||_inf into slot
 __global__ void k_wnorm(const double2* v, const double2* y, double thr, unsigned long long* slots, int idx, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double r[1] = {0.0};
-    if (i < n) {
-        const double2 a = v[i], b = y[i];
-        r[0] = fmax(fabs(a.x) * rcp64<1>(fmax(fabs(b.x), thr)), fabs(a.y) * rcp64<1>(fmax(fabs(b.y), thr)));
-    }
+    if (i < n) r[0] = wnorm_entry(v[i], y[i], thr);
     const int id[1] = {idx};
     block_amax<1>(slots, r, id);
 }

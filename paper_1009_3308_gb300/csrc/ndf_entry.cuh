@@ -4,10 +4,24 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dmath.cuh"
 #include "internal.h"
 #include "newton.cuh"
 
 namespace sph {
+
+// First differences of a new state: D_0 = h F, D_j = 0 for j >= 1
+__device__ __forceinline__ void init_dif_entry(double2* dif, const double2* F, double h, int n, int i) {
+    const double2 f = F[i];
+    dif[i] = make_double2(h * f.x, h * f.y);
+    for (int j = 1; j < SPHNSE_MAXK + 2; ++j) dif[size_t(j) * n + i] = make_double2(0.0, 0.0);
+}
+
+// max(|v.x| / max(|y.x|, thr), |v.y| / max(|y.y|, thr)): one entry of the
+// weighted max-norm of the initial step (FP64, Newton-refined reciprocals)
+__device__ __forceinline__ double wnorm_entry(double2 v, double2 y, double thr) {
+    return fmax(fabs(v.x) * rcp64<1>(fmax(fabs(y.x), thr)), fabs(v.y) * rcp64<1>(fmax(fabs(y.y), thr)));
+}
 
 // D_j <- sum_l A[l][j] D_l for j < k: the differences re-expressed for a new
 // step size (A = R(rho) U, row-major SPHNSE_MAXK x SPHNSE_MAXK)
