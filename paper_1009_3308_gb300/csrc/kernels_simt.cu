@@ -153,7 +153,6 @@ __global__ void __launch_bounds__(128) k_synthesis(const T* __restrict__ psyn, c
     }
     const T inv_s = T(1.0 / sinth[p]);
     const T mm = T(m);
-    const size_t ld = size_t(N + 1);
 #pragma unroll
     for (int hemi = 0; hemi < 2; ++hemi) {
         const int row = hemi == 0 ? p : nlat - 1 - p;

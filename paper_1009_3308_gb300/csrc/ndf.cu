@@ -449,7 +449,7 @@ double sum_partials(sphnse_plan* P, const double* part, int nblk, int* rc) {
     return s;
 }
 
-int stage_launch_check(sphnse_plan* P) { return check_cuda(cudaGetLastError()); }
+int stage_launch_check(sphnse_plan*) { return check_cuda(cudaGetLastError()); }
 
 // rescale the first k differences from h_dif to h (no-op when equal)
 int rescale(sphnse_plan* P, sphnse_state* st, double h, int k) {
