@@ -51,7 +51,8 @@ extern "C" {
 #define SPHNSE_E_STEP_TOO_SMALL   -6  /* the adaptive step fell below 16 eps |t| */
 #define SPHNSE_E_TIMEOUT          -7  /* a bounded device wait ran out */
 #define SPHNSE_E_UNSUPPORTED      -8  /* nlon not 2^a 3^b or above 1536, or a precision not built */
-#define SPHNSE_E_TOO_LARGE        -9  /* size beyond the fixed scratch of an allocation-free entry point */
+#define SPHNSE_E_TOO_LARGE        -9  /* size beyond a fixed capacity: the scratch of an allocation-free
+                                         entry point, the steps a tape was created for */
 
 /* ---- plan parameters (sphnse_plan_set / sphnse_plan_get) ---------------- */
 #define SPHNSE_KEY_PRECISION       1  /* SPHNSE_FP64 | SPHNSE_FP32 | SPHNSE_BF16X3 (default FP64) */
@@ -277,15 +278,73 @@ int sphnse_rhs_adjoint(sphnse_plan* plan, const double* alpha, const double* w,
  * (SPHNSE_MAXK+2) x n_coeff complex) hold the adjoints of (alpha, dif) after
  * the step on entry and before it on return; *nu_bar (host) is accumulated.
  * The transposed corrector system (I - c J^T) mu = dbar_d is solved by
- * fixed-point iteration preconditioned with (I - c J_d)^{-T}. */
-int sphnse_adjoint_step(sphnse_plan* plan, double h, int k, double h_dif_before,
-                        const double* alpha_next, double* abar, double* dbar,
-                        double* nu_bar);
+ * fixed-point iteration preconditioned with (I - c J_d)^{-T}.  The caller
+ * keeps the forward states; sphnse_adjoint_step does this through a tape. */
+int sphnse_adjoint_step_explicit(sphnse_plan* plan, double h, int k, double h_dif_before,
+                                 const double* alpha_next, double* abar, double* dbar,
+                                 double* nu_bar);
 
 /* Reverse of sphnse_state_init: with D_0 = h0 F(alpha0), adds
  * h0 J(alpha0)^T dbar_0 to abar and h0 <dbar_0, dF/dnu> to *nu_bar. */
 int sphnse_adjoint_init(sphnse_plan* plan, double h0, const double* alpha0,
                         double* abar, const double* dbar, double* nu_bar);
+
+/* ---- checkpointed trajectory tape (the map the adjoint differentiates) --- */
+
+/* A tape records the replay of a step schedule [(h_n, k_n)] from alpha0
+ * (frozen controller, each corrector iterated to convergence: the map of
+ * sphnse_replay_step, Sec. 4.2 Eq. (ode_disc)) and drives the reverse sweep.
+ * It keeps every C-th state (alpha, differences, controller scalars) in
+ * device memory it owns, and during the reverse sweep replays one segment of
+ * C steps from its checkpoint to get the states the reverse steps need:
+ * about (1 + ceil(max_steps / C)) (SPHNSE_MAXK + 3) + C + SPHNSE_MAXK + 2
+ * packed vectors of device memory, and one extra forward pass of work. */
+typedef struct sphnse_tape sphnse_tape;
+
+/* Allocate a tape on the plan's device for up to max_steps steps with a
+ * checkpoint every checkpoint_every steps; *tape = NULL on error (E_ARG,
+ * E_NOMEM).  The tape refers to the plan, which must outlive it. */
+int sphnse_tape_create(sphnse_plan* plan, int max_steps, int checkpoint_every, sphnse_tape** tape);
+/* Release the tape (waits for the plan's stream).  NULL is ignored. */
+void sphnse_tape_destroy(sphnse_tape* tape);
+
+/* Start a trajectory at (t0, alpha0) as sphnse_state_init does (h0 <= 0:
+ * automatic initial step).  alpha0 (device, packed) is copied; forcing
+ * (device or NULL) is steady over the trajectory and must stay valid and
+ * unmodified until the reverse sweep ends.  The tape records the plan's nu,
+ * Omega, precision and BDF switch: later recording and reverse calls return
+ * E_ARG if any of them has changed.  Clears any earlier trajectory. */
+int sphnse_tape_begin(sphnse_tape* tape, const double* alpha0, double t0, double h0,
+                      const double* forcing);
+
+/* Append one step of size h and order k (sphnse_replay_step with newton_max
+ * corrector iterations at most); info (host, nullable) as sphnse_replay_step.
+ * E_TOO_LARGE beyond max_steps. */
+int sphnse_tape_record(sphnse_tape* tape, double h, int k, int newton_max, sphnse_step_info* info);
+
+/* Steps recorded, the time reached and the initial step size h0 (host
+ * outputs, any may be NULL). */
+int sphnse_tape_info(const sphnse_tape* tape, int* nsteps, double* t, double* h0);
+
+/* Copy the state after the last recorded step into alpha_out (device, packed). */
+int sphnse_tape_state(const sphnse_tape* tape, double* alpha_out);
+
+/* Reverse of recorded step step_index (discretise-then-differentiate).
+ * lambda (device, packed, in/out): on entry the adjoint of the state after
+ * the step (for step_index = nsteps - 1, dJ/dalpha(t_n) of the objective),
+ * on return the adjoint of the state before it.  *dJ_dnu (host, nullable)
+ * is accumulated with the step's contribution to dJ/dnu.  The tape holds the
+ * adjoint of the difference array between calls, which is why it is not
+ * const.  A sweep starts at step_index = nsteps - 1 (which clears that
+ * adjoint) and must name nsteps - 2, ..., 0 in turn (E_ARG otherwise); the
+ * call for step 0 also applies the reverse of sphnse_state_init, so lambda
+ * then holds dJ/dalpha0.  The first call inside a checkpoint segment replays
+ * the segment forward. */
+int sphnse_adjoint_step(sphnse_plan* plan, sphnse_tape* tape, int step_index, double* lambda,
+                        double* dJ_dnu);
+
+/* The whole reverse sweep: sphnse_adjoint_step for nsteps - 1 down to 0. */
+int sphnse_adjoint_run(sphnse_plan* plan, sphnse_tape* tape, double* lambda, double* dJ_dnu);
 
 /* Final-time objective of a latitude band and a coefficient misfit:
  * J = 1/2 sum over nodes with colatitude in [theta_lo, theta_hi] of

@@ -14,7 +14,7 @@ import math
 from . import _capi
 from ._capi import KEY, MAXK, PRECISION, SphnseError, State, StepInfo, check
 
-__all__ = ["Plan", "Integrator", "Ensemble", "SphnseError", "PRECISION", "MAXK", "n_coeff"]
+__all__ = ["Plan", "Integrator", "Tape", "Ensemble", "SphnseError", "PRECISION", "MAXK", "n_coeff"]
 
 
 def n_coeff(L):
@@ -254,6 +254,77 @@ class Integrator:
             self.plan.handle, ctypes.byref(self.st), _ptr(self.forcing), float(h), int(k), int(newton_max),
             ctypes.byref(info)))
         return info.as_dict()
+
+
+class Tape:
+    """Checkpointed trajectory tape of a plan (sphnse_tape): records the replay
+    of a step schedule and drives the reverse sweep in the library."""
+
+    def __init__(self, plan, max_steps, checkpoint_every=20):
+        h = ctypes.c_void_p()
+        check("sphnse_tape_create", _capi.lib().sphnse_tape_create(plan.handle, int(max_steps),
+                                                                   int(checkpoint_every), ctypes.byref(h)))
+        self._h = h
+        self.plan = plan
+        self._forcing = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _capi.lib().sphnse_tape_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def begin(self, alpha0, t0=0.0, h0=0.0, forcing=None):
+        """Start at (t0, alpha0); h0 <= 0 picks the initial step.  The forcing
+        tensor is kept alive by the tape object until the next begin."""
+        alpha0 = self.plan._coeff(alpha0, "alpha0")
+        self._forcing = self.plan._coeff(forcing, "forcing")
+        self.plan._stream()
+        check("sphnse_tape_begin", _capi.lib().sphnse_tape_begin(self._h, _ptr(alpha0), float(t0), float(h0),
+                                                                 _ptr(self._forcing)))
+
+    def record(self, h, k, newton_max=50):
+        info = StepInfo()
+        self.plan._stream()
+        check("sphnse_tape_record", _capi.lib().sphnse_tape_record(self._h, float(h), int(k), int(newton_max),
+                                                                   ctypes.byref(info)))
+        return info.as_dict()
+
+    def info(self):
+        n, t, h0 = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        check("sphnse_tape_info", _capi.lib().sphnse_tape_info(self._h, ctypes.byref(n), ctypes.byref(t),
+                                                               ctypes.byref(h0)))
+        return dict(nsteps=n.value, t=t.value, h0=h0.value)
+
+    def state(self, out=None):
+        out = self.plan.empty_coeff() if out is None else self.plan._coeff(out, "out")
+        self.plan._stream()
+        check("sphnse_tape_state", _capi.lib().sphnse_tape_state(self._h, _ptr(out)))
+        return out
+
+    def adjoint_step(self, step_index, lam):
+        """Reverse of recorded step step_index on lam (in place); returns its dJ/dnu part."""
+        lam = self.plan._coeff(lam, "lambda")
+        nb = ctypes.c_double(0.0)
+        self.plan._stream()
+        check("sphnse_adjoint_step", _capi.lib().sphnse_adjoint_step(
+            self.plan.handle, self._h, int(step_index), _ptr(lam), ctypes.byref(nb)))
+        return nb.value
+
+    def adjoint_run(self, lam):
+        """The whole reverse sweep on lam (in place: dJ/dalpha(t_n) in,
+        dJ/dalpha0 out); returns dJ/dnu."""
+        lam = self.plan._coeff(lam, "lambda")
+        nb = ctypes.c_double(0.0)
+        self.plan._stream()
+        check("sphnse_adjoint_run", _capi.lib().sphnse_adjoint_run(self.plan.handle, self._h, _ptr(lam),
+                                                                   ctypes.byref(nb)))
+        return nb.value
 
 
 class Ensemble:

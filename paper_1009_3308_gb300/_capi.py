@@ -59,8 +59,19 @@ _SIGS = {
     "sphnse_replay_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.c_double,
                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(StepInfo)]),
     "sphnse_rhs_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p]),
-    "sphnse_adjoint_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p]),
+    "sphnse_adjoint_step_explicit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p]),
+    "sphnse_tape_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "sphnse_tape_destroy": (None, [ctypes.c_void_p]),
+    "sphnse_tape_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_void_p]),
+    "sphnse_tape_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(StepInfo)]),
+    "sphnse_tape_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), c_double_p, c_double_p]),
+    "sphnse_tape_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sphnse_adjoint_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           c_double_p]),
+    "sphnse_adjoint_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p]),
     "sphnse_adjoint_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, c_double_p]),
     "sphnse_objective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,

@@ -911,8 +911,8 @@ int sphnse_adjoint_init(sphnse_plan* P, double h0, const double* alpha0, double*
     return rc ? rc : check_cuda(cudaGetLastError());
 }
 
-int sphnse_adjoint_step(sphnse_plan* P, double h, int k, double h_dif_before, const double* alpha_next,
-                        double* abar, double* dbar, double* nu_bar) {
+int sphnse_adjoint_step_explicit(sphnse_plan* P, double h, int k, double h_dif_before, const double* alpha_next,
+                                 double* abar, double* dbar, double* nu_bar) {
     if (!P || !(h > 0.0) || k < 1 || k > SPHNSE_MAXK || !alpha_next || !abar || !dbar) return SPHNSE_E_ARG;
     const NDFConst C(P->bdf != 0);
     const int n = P->n_coeff;

@@ -13,6 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from _parity import degree_order_errors
 from oracle.rhs import Problem, rhs_separable
 from seeded_inputs import coefficients, workload
 
@@ -37,8 +38,10 @@ def test_rhs_bf16x3_matches_oracle(L, nlon, nu, Om, decay):
     plan = Plan(L, nlon // 2, nlon, nu, Om, precision="bf16x3")
     got = plan.rhs(_dev(a)).cpu().numpy()
     err = _rel(got, ref)
-    print(f"L={L} bf16x3 rel err {err:.3e}")
+    eL, Lw, em, mw = degree_order_errors(got, ref, prob, a, floor=1e-2)
+    print(f"L={L} bf16x3 rel err {err:.3e}; per degree {eL:.2e} (L={Lw}), per order {em:.2e} (m={mw})")
     assert err <= 3e-5, err
+    assert eL <= 1e-3 and em <= 1e-3, (eL, Lw, em, mw)
     assert plan.sync() == 0
 
 

@@ -6,6 +6,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from _parity import degree_order_errors
 from seeded_inputs import coefficients
 
 pytestmark = pytest.mark.gpu
@@ -126,6 +127,9 @@ def test_full_ensemble_rhs_matches_oracle_on_sampled_members(precision, tol):
         got = ens.get(i, "F").cpu().numpy()
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= tol, (i, m["L"], err)
+        prob = Problem(m["L"], m["nlon"], m["nu"], m["Omega"])
+        eL, Lw, em, mw = degree_order_errors(got, ref, prob, m["alpha0"], floor=1e-2)
+        assert eL <= 1e-3 and em <= 1e-3, (i, m["L"], eL, Lw, em, mw)
     for i in range(len(mem)):
         assert torch.isfinite(torch.view_as_real(ens.get(i, "F"))).all(), i
 

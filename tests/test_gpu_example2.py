@@ -1,6 +1,12 @@
 """Sec. 5 Example 2 (N = 100, Omega = 1, nu = 1e-4, rtol 1e-3): the random
-initial state of degree <= 20 driven by fhat_{3,0}(t).  The paper compares
-plots; these checks take the properties it reports in numbers:
+initial state of degree <= 20 driven by fhat_{3,0}(t).
+
+Against the oracle: both adaptive integrators, given the forcing at the end
+of each planned step, take the same orders, rejections and step sizes, and
+reach the same state, from t = 0 and over the switch of fhat_{3,0} at t = 10.
+
+The paper compares plots; the long-run checks take the properties it reports
+in numbers:
 - the initial small structures give way to larger ones (the energy centroid
   of U_75 moves to lower degrees);
 - L^4 E(Phi_150(U_75), L) of the approximate inertial manifold
@@ -13,9 +19,45 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle.ndf import NDF
+from oracle.rhs import Problem, rhs_separable
 from seeded_inputs import example2, example2_forcing_30
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("t0,nsteps", [(0.0, 40), (9.9, 60)])
+def test_example2_steps_match_oracle(t0, nsteps):
+    from paper_1009_3308_gb300 import Integrator, Plan
+    N, nu, rtol = 100, 1e-4, 1e-3
+    a0 = example2(N)
+    atol = 1e-3 * rtol * float(np.abs(a0).max())
+    plan = Plan(N, 162, 324, nu, 1.0)
+    plan.set("RTOL", rtol)
+    plan.set("ATOL", atol)
+    prob = Problem(N, 324, nu, 1.0)
+    fo = np.zeros(prob.n(), dtype=np.complex128)
+    fo[2] = example2_forcing_30(t0)          # packed index of (L, m) = (3, 0)
+    nd = NDF(lambda t, y: rhs_separable(prob, y, fo), -prob.nu * prob.lam + 2j * prob.ms / prob.lam, t0, a0,
+             rtol=rtol, atol=atol)
+    f = torch.from_numpy(fo.copy()).cuda()
+    it = Integrator(plan, torch.from_numpy(a0).cuda(), t0=t0, forcing=f)
+    assert abs(it.h0 - nd.h) <= 1e-12 * nd.h
+    rej = 0
+    for s in range(nsteps):
+        fo[2] = example2_forcing_30(nd.t + nd.h)
+        f[2] = example2_forcing_30(it.t + it.st.h)
+        io = nd.step()
+        ig = it.step()
+        assert ig["order"] == io["order"] and ig["rejections"] == io["rejections"], (s, ig, io)
+        assert abs(ig["h"] - io["h"]) <= 1e-6 * io["h"], (s, ig["h"], io["h"])
+        rej += io["rejections"]
+    err = float(np.linalg.norm(it.alpha.cpu().numpy() - nd.y) / np.linalg.norm(nd.y))
+    print(f"Example 2 from t = {t0}: {nsteps} steps to t = {nd.t:.5f}, {rej} rejections, state rel err {err:.2e}")
+    assert err <= 1e-7
+    assert abs(it.t - nd.t) <= 1e-6 * nd.t
+    if t0 > 0:
+        assert nd.t > 10.0   # the stretch crosses the switch of the forcing
 
 
 def test_example2_large_structures_and_inertial_manifold_decay():

@@ -12,6 +12,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from _parity import degree_order_errors
 from oracle.rhs import Problem, project, rhs_separable, synthesize
 from seeded_inputs import coefficients, random_packed, workload
 
@@ -51,6 +52,9 @@ def test_rhs_fp64_matches_oracle(L, nlon, nu, Om, decay):
     plan = _plan(L, nlon, nu, Om)
     got = plan.rhs(_dev(a), _dev(f)).cpu().numpy()
     assert _rel(got, ref) <= 1e-12, _rel(got, ref)
+    # nonlinear part per degree and per order, above 1e-6 of the largest degree
+    eL, Lw, em, mw = degree_order_errors(got, ref, prob, a, f, floor=1e-6)
+    assert eL <= 1e-8 and em <= 1e-8, (eL, Lw, em, mw)
     # no forcing
     got0 = plan.rhs(_dev(a)).cpu().numpy()
     assert _rel(got0, rhs_separable(prob, a)) <= 1e-12
@@ -78,6 +82,8 @@ def test_rhs_fp32_matches_oracle(L, nlon, nu, Om, decay):
     plan = _plan(L, nlon, nu, Om, "fp32")
     got = plan.rhs(_dev(a)).cpu().numpy()
     assert _rel(got, ref) <= 3e-5, _rel(got, ref)
+    eL, Lw, em, mw = degree_order_errors(got, ref, prob, a, floor=1e-2)
+    assert eL <= 1e-3 and em <= 1e-3, (eL, Lw, em, mw)
 
 
 def test_rhs_invariants_fp64_L255_full_size():
@@ -91,6 +97,8 @@ def test_rhs_invariants_fp64_L255_full_size():
     got = plan.rhs(_dev(a)).cpu().numpy()
     ref = rhs_separable(prob, a)
     assert _rel(got, ref) <= 1e-12, _rel(got, ref)
+    eL, Lw, em, mw = degree_order_errors(got, ref, prob, a, floor=1e-6)
+    assert eL <= 1e-8 and em <= 1e-8, (eL, Lw, em, mw)
     Nn = -(got + prob.nu * prob.lam * a)
     s = np.where(prob.ms == 0, 1.0, 2.0)
     e = np.sum(s * np.conj(a) * Nn).real / (np.linalg.norm(a) * np.linalg.norm(Nn))

@@ -66,8 +66,9 @@ def test_replay_matches_oracle():
 
 
 def test_adaptive_controller_matches_oracle_L31():
-    """The L = 31 workload (rtol 1e-8, steady forcing): both adaptive
-    integrators take the same decisions."""
+    """The L = 31 workload at its stated length (100 adaptive steps, rtol
+    1e-8, steady forcing): both adaptive integrators take the same decisions,
+    and alpha(t_100) agrees."""
     from paper_1009_3308_gb300 import Integrator
     w, c, prob, plan = _l31()
     a0, f = w["alpha0"], w["forcing"]
@@ -78,7 +79,7 @@ def test_adaptive_controller_matches_oracle_L31():
     nd = NDF(lambda t, y: rhs_separable(prob, y, f), _jd(prob), 0.0, a0, rtol=rt, atol=at)
     integ = Integrator(plan, _dev(a0), forcing=_dev(f))
     assert abs(integ.h0 - nd.h) <= 1e-12 * nd.h
-    for s in range(40):
+    for s in range(c["steps"]):
         io = nd.step()
         ig = integ.step()
         assert ig["order"] == io["order"], (s, ig, io)
@@ -87,7 +88,9 @@ def test_adaptive_controller_matches_oracle_L31():
         # F appear amplified (~1e-9 relative) in the chosen step sizes
         assert abs(ig["h"] - io["h"]) <= 1e-6 * io["h"], (s, ig["h"], io["h"])
         assert ig["rejections"] == io["rejections"]
-    assert _rel(integ.alpha.cpu().numpy(), nd.y) <= 1e-7
+    err = _rel(integ.alpha.cpu().numpy(), nd.y)
+    print(f"L=31 after {c['steps']} adaptive steps: t = {nd.t:.6g}, alpha rel err {err:.2e}")
+    assert err <= 1e-7
     assert abs(integ.t - nd.t) <= 1e-6 * nd.t
 
 

@@ -169,6 +169,21 @@ def test_split_coriolis_equals_full_rhs():
     np.testing.assert_allclose(split, full, atol=1e-13 * np.abs(full).max())
 
 
+@pytest.mark.parametrize("N,M,Omega", [(12, 38, 0.0), (31, 96, 1.3)])
+def test_advection_has_no_degree_one_component(N, M, Omega):
+    """The advection term conserves the flow's angular momentum, whose
+    components are the degree-1 coefficients (Z_{1,m} = lambda_1^{-1/2}
+    Curl Y_{1,m} are the solid-body rotations): (B(u,u), Z_{1,m}) = 0 for any
+    u.  At L = 1 only the Coriolis diagonal of Eq. (Coriolis_ZLm) remains."""
+    prob = Problem(N, M, 1e-3, Omega)
+    a = random_packed(N, 77)
+    Nn = _nonlinear(prob, a)
+    cor = -2j * Omega * prob.ms / prob.lam * a
+    one = prob.Ls == 1
+    assert np.linalg.norm((Nn - cor)[one]) <= 1e-14 * np.linalg.norm(Nn)
+    assert np.linalg.norm(Nn[prob.Ls == 2]) > 1e-3 * np.linalg.norm(Nn)
+
+
 # ---------------------------------------------------------------------------
 # planted mistakes: each must be caught by one of the pins above
 
