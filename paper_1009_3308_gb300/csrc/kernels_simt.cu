@@ -10,6 +10,7 @@
 // SPHNSE_FP32); the coefficient state in and out is always FP64.
 #include <cuda_runtime.h>
 
+#include "finish.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -315,33 +316,18 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
     const float4 c = finc[i];
     const float* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
     const float* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
-    float hdr = 0.f, hdi = 0.f;
-    if (L - 1 >= m) {
-        const float* hD = hana + size_t(ext_row(N, m, L - 1)) * 2 * nf;
-        hdr = hD[2];
-        hdi = hD[3];
-    }
-    const float cm = c.x * float(m);
-    const float nr = cm * hL[1] - (c.y * hU[2] - c.z * hdr);
-    const float ni = -cm * hL[0] - (c.y * hU[3] - c.z * hdi);
-    const double lam = double(L) * double(L + 1);
+    const float* hD = L - 1 >= m ? hana + size_t(ext_row(N, m, L - 1)) * 2 * nf : nullptr;
     double2 r;
-    if (kind == 0) {
-        const double2 a = alpha[i];
-        const double2 f = forcing ? forcing[i] : make_double2(0.0, 0.0);
-        const double nl = nu * lam;
-        r.x = fma(-nl, a.x, f.x) - double(nr);
-        r.y = fma(-nl, a.y, f.y) - double(ni);
-        if (omega_d != 0.0) {
-            // 2 Omega m / lambda from lambda^{-1/2} in FP32 (relative 1e-7, below
-            // the FP32 and BF16x3 paths' own error); FP64 divides are slow here
-            const double cor = double(2.f * float(omega_d) * float(m) * c.x * c.x);
-            r.x = fma(-cor, a.y, r.x);
-            r.y = fma(cor, a.x, r.y);
-        }
-    } else if (kind == 1) {
-        r = make_double2(double(nr), double(ni));
+    if (kind < 2) {
+        const double2 a = kind == 0 ? alpha[i] : make_double2(0.0, 0.0);
+        const double2 f = kind == 0 && forcing ? forcing[i] : make_double2(0.0, 0.0);
+        r = finish32_entry(kind, L, m, c, hL, hU, hD, a, f, nu, omega_d);
     } else {
+        const float hdr = hD ? hD[2] : 0.f, hdi = hD ? hD[3] : 0.f;
+        const float cm = c.x * float(m);
+        const float nr = cm * hL[1] - (c.y * hU[2] - c.z * hdr);
+        const float ni = -cm * hL[0] - (c.y * hU[3] - c.z * hdi);
+        const double lam = double(L) * double(L + 1);
         const double2 wv = alpha[i];
         const float sm = m == 0 ? 1.f : 2.f;
         const float sl = c.w * c.x;  // lambda^{1/2}

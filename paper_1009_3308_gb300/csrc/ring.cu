@@ -23,88 +23,12 @@
 
 #include <cmath>
 
+#include "fft_small.cuh"
 #include "internal.h"
 #include "ptx.cuh"
+#include "ring4.cuh"
 
 namespace sph {
-
-template <typename T> struct cx { T x, y; };
-
-template <typename T>
-__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-
-template <typename T, typename TW>
-__device__ __forceinline__ cx<T> twiddle(const TW* tw, int t, int sign) {
-    // tw holds e^{-2 pi i t / M}; the inverse transform (sign = +1) uses its conjugate
-    cx<T> w{T(tw[2 * t]), T(tw[2 * t + 1])};
-    if (sign > 0) w.y = -w.y;
-    return w;
-}
-
-// small DFTs: y_r = sum_s v_s e^{sign 2 pi i r s / R}
-template <typename T>
-__device__ __forceinline__ void dft2(cx<T>* v) {
-    cx<T> a = v[0], b = v[1];
-    v[0] = {a.x + b.x, a.y + b.y};
-    v[1] = {a.x - b.x, a.y - b.y};
-}
-template <typename T>
-__device__ __forceinline__ void dft3(cx<T>* v, int sign) {
-    const T h = T(0.86602540378443864676);  // sqrt(3)/2
-    cx<T> t1{v[1].x + v[2].x, v[1].y + v[2].y};
-    cx<T> t2{v[0].x - T(0.5) * t1.x, v[0].y - T(0.5) * t1.y};
-    cx<T> t3{T(sign) * h * (v[1].x - v[2].x), T(sign) * h * (v[1].y - v[2].y)};
-    v[0] = {v[0].x + t1.x, v[0].y + t1.y};
-    v[1] = {t2.x - t3.y, t2.y + t3.x};  // t2 + i t3
-    v[2] = {t2.x + t3.y, t2.y - t3.x};  // t2 - i t3
-}
-template <typename T>
-__device__ __forceinline__ void dft4(cx<T>* v, int sign) {
-    cx<T> a0{v[0].x + v[2].x, v[0].y + v[2].y};
-    cx<T> a1{v[0].x - v[2].x, v[0].y - v[2].y};
-    cx<T> b0{v[1].x + v[3].x, v[1].y + v[3].y};
-    cx<T> b1{v[1].x - v[3].x, v[1].y - v[3].y};
-    // (sign i) * b1
-    cx<T> ib1{-T(sign) * b1.y, T(sign) * b1.x};
-    v[0] = {a0.x + b0.x, a0.y + b0.y};
-    v[2] = {a0.x - b0.x, a0.y - b0.y};
-    v[1] = {a1.x + ib1.x, a1.y + ib1.y};
-    v[3] = {a1.x - ib1.x, a1.y - ib1.y};
-}
-
-// radix 8 = two radix-4 DFTs of the even/odd samples and a radix-2 combine
-// with the eighth roots of unity w^r = e^{sign 2 pi i r / 8}
-template <typename T>
-__device__ __forceinline__ void dft8(cx<T>* v, int sign) {
-    cx<T> e[4] = {v[0], v[2], v[4], v[6]};
-    cx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    dft4(e, sign);
-    dft4(o, sign);
-    const T h = T(0.70710678118654752440);  // sqrt(2)/2
-    const T sg = T(sign);
-    // w^1 = h (1, sign), w^2 = (0, sign), w^3 = h (-1, sign)
-    cx<T> t1{h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x)};
-    cx<T> t2{-sg * o[2].y, sg * o[2].x};
-    cx<T> t3{h * (-o[3].x - sg * o[3].y), h * (-o[3].y + sg * o[3].x)};
-    v[0] = {e[0].x + o[0].x, e[0].y + o[0].y};
-    v[4] = {e[0].x - o[0].x, e[0].y - o[0].y};
-    v[1] = {e[1].x + t1.x, e[1].y + t1.y};
-    v[5] = {e[1].x - t1.x, e[1].y - t1.y};
-    v[2] = {e[2].x + t2.x, e[2].y + t2.y};
-    v[6] = {e[2].x - t2.x, e[2].y - t2.y};
-    v[3] = {e[3].x + t3.x, e[3].y + t3.y};
-    v[7] = {e[3].x - t3.x, e[3].y - t3.y};
-}
-
-template <typename T, int R>
-__device__ __forceinline__ void dft(cx<T>* v, int sign) {
-    if constexpr (R == 8) dft8(v, sign);
-    else if constexpr (R == 4) dft4(v, sign);
-    else if constexpr (R == 2) dft2(v);
-    else dft3(v, sign);
-}
 
 // One in-place Stockham stage of radix R over NSIG signals (buf[s], M points):
 // every thread first reads and transforms all of its butterflies into
@@ -357,337 +281,15 @@ int launch_ring(sphnse_plan* P, int mode, int prec, const double* gin0, const do
 }
 
 // ---------------------------------------------------------------------------
-// Four-step ring kernel for M = 24 M2 (M2 = 4 .. 64), FP32, RHS mode, reading
-// the synthesis output (order-major or latitude-pair-major) and writing the
-// order-major spectra of the analysis directly, without transposes.
-//
-// With n = t + M2 n1 and k = k1 + 24 k2 (t, k2 < M2; n1, k1 < 24), and
-// t = b + B a', k2 = c + A d (M2 = A B):
-//   pass 1  (thread t):       24-point DFT over n1, twiddle e^{s 2 pi i t k1 / M}
-//   pass 2a (task (k1, b)):   A-point DFT over a', twiddle e^{s 2 pi i b c / M2}
-//   pass 2b (task (k1, c)):   B-point DFT over b -> X[k1 + 24 (c + A d)]
-// Every thread keeps 24 complex values per signal in registers; the passes
-// exchange through padded shared-memory tiles whose strides make every warp
-// access conflict-free (B > 1: M2 = 64, 16; one 2-way pass at M2 = 32).
-// The pointwise product is taken in the registers of pass 2b, and the forward
-// transform of W runs the same factorisation backwards (DFT matrices are
-// symmetric): B-point DFT over d, A-point DFT over c, 24-point DFT over k1,
-// which leaves W's spectrum in natural order across the threads of pass 1.
-// One CTA of 128 threads holds G = 128 / M2 consecutive rings, so every
-// order-major access moves G consecutive latitudes (>= 16 bytes).
-
-template <int M2> struct R4;
-template <> struct R4<64> { static constexpr int A = 8, P1 = 72, Bp = 9, Q = 72, RING = 1728; };
-template <> struct R4<32> { static constexpr int A = 8, P1 = 36, Bp = 5, Q = 40, RING = 960; };
-template <> struct R4<16> { static constexpr int A = 4, P1 = 20, Bp = 5, Q = 20, RING = 480; };
-template <> struct R4<8> { static constexpr int A = 8, P1 = 9, Bp = 1, Q = 9, RING = 216; };
-template <> struct R4<4> { static constexpr int A = 4, P1 = 5, Bp = 1, Q = 5, RING = 124; };
-
-// cos, sin of 2 pi j / 24, j = 0..14
-__device__ constexpr double kC24[15] = {1.0, 0.96592582628906828675, 0.86602540378443864676, 0.7071067811865475244,
-                                        0.5, 0.25881904510252076235, 0.0, -0.25881904510252076235, -0.5,
-                                        -0.7071067811865475244, -0.86602540378443864676, -0.96592582628906828675,
-                                        -1.0, -0.96592582628906828675, -0.86602540378443864676};
-__device__ constexpr double kS24[15] = {0.0, 0.25881904510252076235, 0.5, 0.7071067811865475244,
-                                        0.86602540378443864676, 0.96592582628906828675, 1.0, 0.96592582628906828675,
-                                        0.86602540378443864676, 0.7071067811865475244, 0.5, 0.25881904510252076235,
-                                        0.0, -0.25881904510252076235, -0.5};
-
-// 24-point DFT in registers, natural order in and out: n = 3 n1 + n2,
-// k = k1 + 8 k2 (three 8-point DFTs, twiddles e^{s 2 pi i n2 k1 / 24}, eight
-// 3-point DFTs)
-template <int S, typename T>
-__device__ __forceinline__ void dft24(cx<T>* x) {
-    cx<T> u[3][8];
-#pragma unroll
-    for (int n2 = 0; n2 < 3; ++n2) {
-#pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) u[n2][n1] = x[3 * n1 + n2];
-        dft8(u[n2], S);
-    }
-#pragma unroll
-    for (int n2 = 1; n2 < 3; ++n2)
-#pragma unroll
-        for (int k1 = 1; k1 < 8; ++k1) {
-            const int j = n2 * k1;
-            u[n2][k1] = cmul(u[n2][k1], cx<T>{T(kC24[j]), T(S * kS24[j])});
-        }
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) {
-        cx<T> v[3] = {u[0][k1], u[1][k1], u[2][k1]};
-        dft3(v, S);
-#pragma unroll
-        for (int k2 = 0; k2 < 3; ++k2) x[k1 + 8 * k2] = v[k2];
-    }
-}
-
-template <int R, typename T>
-__device__ __forceinline__ void dftn(cx<T>* v, int sign) {
-    if constexpr (R > 1) dft<T, R>(v, sign);
-}
-
-__device__ __forceinline__ cx<float> ld2(const float2* p) {
-    const float2 v = *p;
-    return {v.x, v.y};
-}
-__device__ __forceinline__ void st2(float2* p, cx<float> v) { *p = make_float2(v.x, v.y); }
-__device__ __forceinline__ cx<float> conjf2(float2 v) { return {v.x, -v.y}; }
-
-struct Ring4Args {
-    int N, nlat;
-    float two_omega;
-    const double* x;       // cos(theta)
-    const double* rw;      // (2 pi / M) w_p / sin(theta_p)
-    const float2* gsyn;    // three complex spectra, layout gsyn_index(pairs, ...)
-    float2* gana;          // [2][N+1][nlat] complex (order-major)
-    const float2* ftw;     // tw1 [24][P1] = e^{+2 pi i t k1 / M}, then tw2 [A][B+1] = e^{+2 pi i b c / M2}
-    size_t sgs, sga;       // per-instance strides (complex entries) along gridDim.y
-    int pairs;             // input layout: latitude-pair-major (1) or order-major (0)
-};
+// Four-step ring kernel (the transform itself is in ring4.cuh)
 
 template <int M2>
-__global__ void __launch_bounds__(128, 3) k_ring4(Ring4Args a) {
-    using C = R4<M2>;
-    constexpr int M = 24 * M2, A = C::A, B = M2 / A, P1 = C::P1, Bp = C::Bp, Q = C::Q, RING = C::RING;
-    constexpr int G = 128 / M2, GP = G / 2, B2 = B + 1;
-    constexpr int TA = 24 / A, TB = 24 / B;
+__global__ void __launch_bounds__(128, 4) k_ring4(Ring4Args a) {
     extern __shared__ __align__(16) float2 sm4[];
-    float2* tw1 = sm4;
-    float2* tw2 = tw1 + 24 * P1;
-    float2* buf = tw2 + ((A * B2 + 1) & ~1);
-    // twiddles do not depend on the predecessor: stage them before waiting for it,
-    // with all of a thread's loads issued before its stores
-    constexpr int NTW = (24 * P1 + A * B2 + 127) / 128;
-    {
-        float2 tv[NTW];
-#pragma unroll
-        for (int k = 0; k < NTW; ++k) {
-            const int i = threadIdx.x + 128 * k;
-            tv[k] = i < 24 * P1 + A * B2 ? __ldg(a.ftw + i) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int k = 0; k < NTW; ++k) {
-            const int i = threadIdx.x + 128 * k;
-            if (i < 24 * P1 + A * B2) tw1[i] = tv[k];
-        }
-    }
+    __shared__ float s_rw[128 / M2];
     pdl_launch();
     pdl_wait();
-    const int N = a.N, nlat = a.nlat, ld = N + 1;
-    const int lat0 = blockIdx.x * G;
-    const float2* gs = a.gsyn + size_t(blockIdx.y) * a.sgs;
-    float2* ga = a.gana + size_t(blockIdx.y) * a.sga;
-
-    // stage the spectra: ring r, field f, order m -> buf[r RING + f (N+1) + m].
-    // In the latitude-pair-major input, [f][row / 2][m][row % 2], the CTA's
-    // pairs are contiguous runs of (N+1) float4 per field; the order-major
-    // input gives one float4 per (f, m).  3 (N+1) G / 2 <= 1536 float4 loads
-    // per CTA, all of a thread's issued before its stores.
-    constexpr int NLD = (3 * 8 * M2 * GP + 127) / 128;
-    float4 stv[NLD];
-#pragma unroll
-    for (int k = 0; k < NLD; ++k) {
-        const int i = threadIdx.x + 128 * k;
-        const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
-        const int pr = lat0 / 2 + rp;
-        stv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < 3 * ld * GP && 2 * pr < nlat)
-            stv[k] = __ldcs(reinterpret_cast<const float4*>(gs + gsyn_index(a.pairs, f, m, 2 * pr, N, nlat)));
-    }
-    const int r = threadIdx.x / M2, t = threadIdx.x % M2;
-    const int lat = lat0 + r;
-    const float fc = lat < nlat ? a.two_omega * float(a.x[lat]) : 0.f;
-    __shared__ float s_rw[G];
-    if (threadIdx.x < G) s_rw[threadIdx.x] = lat0 + int(threadIdx.x) < nlat ? float(a.rw[lat0 + threadIdx.x]) : 0.f;
-#pragma unroll
-    for (int k = 0; k < NLD; ++k) {
-        const int i = threadIdx.x + 128 * k;
-        if (i < 3 * ld * GP) {
-            const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
-            buf[(2 * rp) * RING + f * ld + m] = make_float2(stv[k].x, stv[k].y);
-            buf[(2 * rp + 1) * RING + f * ld + m] = make_float2(stv[k].z, stv[k].w);
-        }
-    }
-    __syncthreads();
-    float2* XA = buf + r * RING;
-    float2* XB = buf + (G + r) * RING;
-
-    // pass 1: Hermitian spectra packed as A = zeta + i u_theta, B = u_phi.
-    // With M >= 3N + 2, n = t + M2 n1 lies in (N, M - N) for n1 = 8 .. 15, so
-    // those inputs are zero for every thread (compile-time, folded into dft24)
-    cx<float> xa[24], xb[24];
-#pragma unroll
-    for (int n1 = 0; n1 < 24; ++n1) {
-        const int n = t + M2 * n1;
-        cx<float> za{0.f, 0.f}, zb{0.f, 0.f};
-        if (n1 >= 8 && n1 < 16) {
-        } else if (n <= N) {
-            float2 g0 = XA[n], g1 = XA[ld + n], g2 = XA[2 * ld + n];
-            if (n == 0) g0.y = g1.y = g2.y = 0.f;
-            za = {g0.x - g1.y, g0.y + g1.x};
-            zb = {g2.x, g2.y};
-        } else if (n >= M - N) {
-            const int mm = M - n;
-            const float2 g0 = XA[mm], g1 = XA[ld + mm], g2 = XA[2 * ld + mm];
-            za = {g0.x + g1.y, g1.x - g0.y};
-            zb = {g2.x, -g2.y};
-        }
-        xa[n1] = za;
-        xb[n1] = zb;
-    }
-    dft24<+1>(xa);
-    dft24<+1>(xb);
-#pragma unroll
-    for (int k1 = 1; k1 < 24; ++k1) {
-        const cx<float> w = ld2(&tw1[k1 * P1 + t]);
-        xa[k1] = cmul(xa[k1], w);
-        xb[k1] = cmul(xb[k1], w);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k1 = 0; k1 < 24; ++k1) {
-        st2(&XA[k1 * P1 + t], xa[k1]);
-        st2(&XB[k1 * P1 + t], xb[k1]);
-    }
-    __syncthreads();
-
-    // pass 2a: task (k1 = j A + kq, b)
-    const int b = t % B, kq = t / B;
-    cx<float> ua[TA][A], ub[TA][A];
-#pragma unroll
-    for (int j = 0; j < TA; ++j) {
-        const int k1 = j * A + kq;
-#pragma unroll
-        for (int ap = 0; ap < A; ++ap) {
-            ua[j][ap] = ld2(&XA[k1 * P1 + b + B * ap]);
-            ub[j][ap] = ld2(&XB[k1 * P1 + b + B * ap]);
-        }
-        dftn<A>(ua[j], +1);
-        dftn<A>(ub[j], +1);
-        if constexpr (B > 1) {
-#pragma unroll
-            for (int c = 1; c < A; ++c) {
-                const cx<float> w = ld2(&tw2[c * B2 + b]);
-                ua[j][c] = cmul(ua[j][c], w);
-                ub[j][c] = cmul(ub[j][c], w);
-            }
-        }
-    }
-    auto product = [&](cx<float>& za, const cx<float>& zb) {
-        // zeta = Re A, u_theta = Im A, u_phi = Re B;  W = (-q u_phi, q u_theta)
-        const float q = za.x + fc;
-        za = {-q * zb.x, q * za.y};
-    };
-
-    if constexpr (B > 1) {
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < TA; ++j) {
-            const int k1 = j * A + kq;
-#pragma unroll
-            for (int c = 0; c < A; ++c) {
-                st2(&XA[k1 * Q + c * Bp + b], ua[j][c]);
-                st2(&XB[k1 * Q + c * Bp + b], ub[j][c]);
-            }
-        }
-        __syncthreads();
-        // pass 2b: task (k1 = j B + kq2, c) -> X[k1 + 24 (c + A d)]
-        const int c = t % A, kq2 = t / A;
-        cx<float> va[TB][B], vb[TB][B];
-#pragma unroll
-        for (int j = 0; j < TB; ++j) {
-            const int k1 = j * B + kq2;
-#pragma unroll
-            for (int bb = 0; bb < B; ++bb) {
-                va[j][bb] = ld2(&XA[k1 * Q + c * Bp + bb]);
-                vb[j][bb] = ld2(&XB[k1 * Q + c * Bp + bb]);
-            }
-            dftn<B>(va[j], +1);
-            dftn<B>(vb[j], +1);
-#pragma unroll
-            for (int d = 0; d < B; ++d) product(va[j][d], vb[j][d]);
-            // forward, backwards through the factorisation: B-point DFT over d
-            dftn<B>(va[j], -1);
-#pragma unroll
-            for (int bb = 1; bb < B; ++bb) va[j][bb] = cmul(va[j][bb], conjf2(tw2[c * B2 + bb]));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < TB; ++j) {
-            const int k1 = j * B + kq2;
-#pragma unroll
-            for (int bb = 0; bb < B; ++bb) st2(&XA[k1 * Q + c * Bp + bb], va[j][bb]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < TA; ++j) {
-            const int k1 = j * A + kq;
-#pragma unroll
-            for (int cc = 0; cc < A; ++cc) ua[j][cc] = ld2(&XA[k1 * Q + cc * Bp + b]);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < TA; ++j)
-#pragma unroll
-            for (int cc = 0; cc < A; ++cc) product(ua[j][cc], ub[j][cc]);
-    }
-    // A-point DFT over c -> a', twiddle e^{-2 pi i t k1 / M} with t = b + B a'
-#pragma unroll
-    for (int j = 0; j < TA; ++j) {
-        const int k1 = j * A + kq;
-        dftn<A>(ua[j], -1);
-#pragma unroll
-        for (int ap = 0; ap < A; ++ap) ua[j][ap] = cmul(ua[j][ap], conjf2(tw1[k1 * P1 + b + B * ap]));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < TA; ++j) {
-        const int k1 = j * A + kq;
-#pragma unroll
-        for (int ap = 0; ap < A; ++ap) st2(&XA[k1 * P1 + b + B * ap], ua[j][ap]);
-    }
-    __syncthreads();
-    // 24-point DFT over k1 -> W's spectrum at n = t + M2 n1
-    cx<float> y[24];
-#pragma unroll
-    for (int k1 = 0; k1 < 24; ++k1) y[k1] = ld2(&XA[k1 * P1 + t]);
-    dft24<-1>(y);
-    __syncthreads();
-    // only m <= N and m >= M - N are read back: n1 = 8 .. 15 are never needed
-#pragma unroll
-    for (int n1 = 0; n1 < 24; ++n1)
-        if (n1 < 8 || n1 >= 16) st2(&XA[t + M2 * n1], y[n1]);
-    __syncthreads();
-
-    // separate the two real fields, truncate to m <= N, weight, store
-    for (int i = threadIdx.x; i < ld * GP; i += 128) {
-        const int rp = i % GP, m = i / GP;
-        const int l = lat0 + 2 * rp;
-        if (l >= nlat) continue;
-        float4 oA, oB;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float2* Z = buf + (2 * rp + e) * RING;
-            const float2 p = Z[m], q = Z[(M - m) % M];
-            const float sc = s_rw[2 * rp + e];
-            const float ax = 0.5f * (p.x + q.x) * sc, ay = 0.5f * (p.y - q.y) * sc;
-            const float bx = 0.5f * (p.y + q.y) * sc, by = 0.5f * (q.x - p.x) * sc;
-            if (e == 0) {
-                oA.x = ax; oA.y = ay; oB.x = bx; oB.y = by;
-            } else {
-                oA.z = ax; oA.w = ay; oB.z = bx; oB.w = by;
-            }
-        }
-        *reinterpret_cast<float4*>(ga + size_t(m) * nlat + l) = oA;
-        *reinterpret_cast<float4*>(ga + size_t(ld + m) * nlat + l) = oB;
-    }
-}
-
-template <int M2>
-static constexpr size_t ring4_smem() {
-    using C = R4<M2>;
-    constexpr int A = C::A, B = M2 / A, G = 128 / M2;
-    return (size_t(24) * C::P1 + ((A * (B + 1) + 1) & ~1) + size_t(2) * G * C::RING) * sizeof(float2);
+    ring4_rings<M2>(a, blockIdx.x * (128 / M2), blockIdx.y, threadIdx.x, sm4, s_rw, [] { __syncthreads(); });
 }
 
 template <int M2>

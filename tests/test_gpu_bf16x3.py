@@ -169,3 +169,4 @@ def test_bf16x3_plan_off_the_tensor_core_grid(L, nlon):
     err = _rel(got, ref)
     print(f"L={L} nlon={nlon} bf16x3 plan rel err {err:.2e}")
     assert err <= 3e-5, err
+
