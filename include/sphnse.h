@@ -74,9 +74,14 @@ extern "C" {
 #define SPHNSE_KEY_TIMING_PERIOD  11  /* stage timing records every period-th launch of a
                                          timed stage (default 1) */
 #define SPHNSE_KEY_AUTOTUNE       12  /* ensemble: 1 (default) times the candidate shapes of
-                                        * the tensor-core synthesis per truncation when BF16X3
+                                        * the tensor-core synthesis per truncation (instances per
+                                        * group, pipeline stages, CTAs per cluster) when BF16X3
                                         * is selected and keeps the fastest (sphnse_ensemble_bucket);
                                         * 0 takes the widest instance groups; set it first */
+#define SPHNSE_KEY_SYN_CLUSTER    14  /* ensemble, with SPHNSE_KEY_AUTOTUNE 0: CTAs per cluster of
+                                         the batched tensor-core synthesis (1 default, 2, 4); the
+                                         CTAs of a cluster take consecutive instance groups and
+                                         share every table tile by TMA multicast.  Set it first */
 #define SPHNSE_KEY_N_COEFF       100  /* read-only: n_coeff */
 #define SPHNSE_KEY_L             101  /* read-only: truncation degree */
 #define SPHNSE_KEY_NLAT          102  /* read-only */
@@ -386,10 +391,11 @@ int sphnse_ensemble_instance(sphnse_ensemble* ens, int i, double** alpha, double
 /* Bucket b (0 .. SPHNSE_KEY_BUCKETS - 1; instances of one truncation share its
  * Legendre tables): its truncation L, instance count, and on the BF16X3
  * tensor-core path the shape of its synthesis (instances per group, pipeline
- * stages) and that synthesis' duration in microseconds as timed by the
- * autotuner (0 when not tuned; group = stages = 0 off the tensor-core path).
- * Any output may be NULL. */
-int sphnse_ensemble_bucket(sphnse_ensemble* ens, int b, int* L, int* count, int* group, int* stages,
+ * stages, CTAs per cluster that share every table tile by TMA multicast) and
+ * that synthesis' duration in microseconds as timed by the autotuner (0 when
+ * not tuned; group = stages = cluster = 0 off the tensor-core path).  Any
+ * output may be NULL. */
+int sphnse_ensemble_bucket(sphnse_ensemble* ens, int b, int* L, int* count, int* group, int* stages, int* cluster,
                            double* syn_us);
 
 /* F_i = F(alpha_i) for every instance (Eq. (ode)), as one CUDA-graph launch. */

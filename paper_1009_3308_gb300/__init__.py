@@ -330,7 +330,7 @@ class Tape:
 class Ensemble:
     """Batched ensemble of independent problems (sphnse_ensemble)."""
 
-    def __init__(self, Ls, nus, Omega, device=None, precision="fp32", autotune=True):
+    def __init__(self, Ls, nus, Omega, device=None, precision="fp32", autotune=True, cluster=1):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libsphnse runs on a CUDA device; none is available")
@@ -347,21 +347,23 @@ class Ensemble:
         self.n = n
         self.Ls = list(Ls)
         self.set("AUTOTUNE", 1 if autotune else 0)
+        self.set("SYN_CLUSTER", cluster)
         if precision != "fp32":
             self.set_precision(precision)
 
     def buckets(self):
         """Per truncation bucket: L, instances, and on the tensor-core path the
-        synthesis shape (instances per group, pipeline stages) with its tuned
-        duration in microseconds."""
+        synthesis shape (instances per group, pipeline stages, CTAs per
+        cluster) with its tuned duration in microseconds."""
         out = []
         for b in range(int(self.get("BUCKETS"))):
-            L, cnt, grp, st = (ctypes.c_int() for _ in range(4))
+            L, cnt, grp, st, cl = (ctypes.c_int() for _ in range(5))
             us = ctypes.c_double()
             check("sphnse_ensemble_bucket", _capi.lib().sphnse_ensemble_bucket(
                 self._h, b, ctypes.byref(L), ctypes.byref(cnt), ctypes.byref(grp), ctypes.byref(st),
-                ctypes.byref(us)))
-            out.append(dict(L=L.value, instances=cnt.value, group=grp.value, stages=st.value, syn_us=us.value))
+                ctypes.byref(cl), ctypes.byref(us)))
+            out.append(dict(L=L.value, instances=cnt.value, group=grp.value, stages=st.value, cluster=cl.value,
+                            syn_us=us.value))
         return out
 
     def set_precision(self, precision):

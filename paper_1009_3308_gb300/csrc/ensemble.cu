@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -309,6 +310,7 @@ struct sphnse_ensemble {
     long rounds = 0;                 // rounds of the last advance
     bool inited = false;             // sphnse_ensemble_init has set the controllers up
     bool autotune = true;            // time the tensor-core synthesis shapes per bucket
+    int syn_cluster = 1;             // without the autotuner: CTAs per cluster of the batched synthesis
 };
 
 namespace {
@@ -620,13 +622,16 @@ static int tune_synthesis(sphnse_ensemble* E, Bucket& B) {
     }
     TcBatch best;
     float best_ms = 0.f;
-    std::vector<std::pair<int, int>> seen;
+    std::vector<std::array<int, 3>> seen;
     int rc = SPHNSE_OK;
-    for (int ng = 1; ng <= std::min(B.nb, 9) && !rc; ++ng)
+    for (int cs = 1; cs <= 4 && !rc; cs *= 2)
+        for (int ng = 1; ng <= std::min(B.nb, 9) && !rc; ++ng)
         for (int ns = 6; ns >= 4 && !rc; --ns) {
             TcBatch T;
-            if ((rc = tc_batch_init(P, B.nb, &T, ng, ns))) break;
-            const std::pair<int, int> shape(T.ng, T.ns);
+            const int irc = tc_batch_init(P, B.nb, &T, ng, ns, cs);
+            if (irc == SPHNSE_E_UNSUPPORTED) continue;   // no resident cluster of this shape
+            if ((rc = irc)) break;
+            const std::array<int, 3> shape{T.ng, T.ns, T.cs};
             if (T.ns < 4 || std::find(seen.begin(), seen.end(), shape) != seen.end()) {
                 tc_batch_free(&T);
                 continue;
@@ -667,7 +672,7 @@ static int set_precision(sphnse_ensemble* E, int prec) {
         if (want && !B.tcb.btiles) {
             int rc = ensure_tables(B.P, SPHNSE_BF16X3);
             if (!rc) rc = tc_setup_synthesis(B.P);
-            if (!rc) rc = E->autotune ? tune_synthesis(E, B) : tc_batch_init(B.P, B.nb, &B.tcb);
+            if (!rc) rc = E->autotune ? tune_synthesis(E, B) : tc_batch_init(B.P, B.nb, &B.tcb, 9, 6, E->syn_cluster);
             if (!rc) rc = tc_batch_ana_init(B.P, B.nb, &B.tca);
             if (rc) return rc;
         }
@@ -690,6 +695,10 @@ int sphnse_ensemble_set(sphnse_ensemble* E, int key, double v) {
         case SPHNSE_KEY_H_MAX: if (v <= 0) return SPHNSE_E_ARG; E->h_max = v; return SPHNSE_OK;
         case SPHNSE_KEY_PRECISION: return set_precision(E, int(v));
         case SPHNSE_KEY_AUTOTUNE: if (v != 0 && v != 1) return SPHNSE_E_ARG; E->autotune = v != 0; return SPHNSE_OK;
+        case SPHNSE_KEY_SYN_CLUSTER:
+            if (v != 1 && v != 2 && v != 4) return SPHNSE_E_ARG;
+            E->syn_cluster = int(v);
+            return SPHNSE_OK;
         default: return SPHNSE_E_ARG;
     }
 }
@@ -719,7 +728,7 @@ int sphnse_ensemble_instance(sphnse_ensemble* E, int i, double** alpha, double**
     return SPHNSE_OK;
 }
 
-int sphnse_ensemble_bucket(sphnse_ensemble* E, int b, int* L, int* count, int* group, int* stages,
+int sphnse_ensemble_bucket(sphnse_ensemble* E, int b, int* L, int* count, int* group, int* stages, int* cluster,
                            double* syn_us) {
     if (!E || b < 0 || b >= int(E->buckets.size())) return SPHNSE_E_ARG;
     const Bucket& B = E->buckets[size_t(b)];
@@ -727,6 +736,7 @@ int sphnse_ensemble_bucket(sphnse_ensemble* E, int b, int* L, int* count, int* g
     if (count) *count = B.nb;
     if (group) *group = B.tc ? B.tcb.ng : 0;
     if (stages) *stages = B.tc ? B.tcb.ns : 0;
+    if (cluster) *cluster = B.tc ? B.tcb.cs : 0;
     if (syn_us) *syn_us = B.tc ? B.syn_us : 0.0;
     return SPHNSE_OK;
 }

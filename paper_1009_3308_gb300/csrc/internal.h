@@ -93,6 +93,7 @@ struct Tables {
 // the LPT item schedule (m, latitude tile, group).
 struct TcBatch {
     int nb = 0, ng = 0, ngroups = 0, brows = 0, ns = 0, ncta = 0;
+    int cs = 1;                        // CTAs per cluster sharing every table tile (multicast)
     unsigned char* btiles = nullptr;   // [group][tile][brows][64] bf16, swizzled
     int4* items = nullptr;
     int* off = nullptr;
@@ -169,6 +170,11 @@ struct TcState {
     bool ana_ready = false;
     void* smap_hi = nullptr;     // synthesis: tensor maps of the transposed tables
     void* smap_lo = nullptr;
+    void* smap_hi_c2 = nullptr;  // the same with boxes of 64 and 32 latitudes (cluster slices)
+    void* smap_lo_c2 = nullptr;
+    void* smap_hi_c4 = nullptr;
+    void* smap_lo_c4 = nullptr;
+    std::vector<size_t> tsyn_off;   // element offset of every block in the transposed tables
     void* tsyn_hi = nullptr;     // transposed padded bf16 tables [block][nh][pad8(n)]
     void* tsyn_lo = nullptr;
     int* tile_off = nullptr;     // first B tile of block (m, parity)
@@ -303,7 +309,7 @@ int launch_prep_tc(sphnse_plan* P, const double* alpha);
 int tc_setup_synthesis(sphnse_plan* P);
 // instance groups of at most ngmax (<= 9) instances, at most nsmax (<= 6)
 // pipeline stages (fewer when the shared memory does not hold them)
-int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax = 9, int nsmax = 6);
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax = 9, int nsmax = 6, int cs = 1);
 void tc_batch_free(TcBatch* B);
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha);
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs);

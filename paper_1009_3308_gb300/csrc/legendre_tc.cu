@@ -547,6 +547,9 @@ struct TcSynArgs {
     size_t sgs;
     const int* kt0;              // first K tile per (block, latitude tile): [2 (N+1)][nmt]
     int nmt;
+    // clusters of CS > 1 CTAs: maps of the same blocks with boxes of 128 / CS latitudes
+    const CUtensorMap* map_hi_cs;
+    const CUtensorMap* map_lo_cs;
 };
 
 constexpr int TC_SYN_MAXNS = 8;
@@ -572,8 +575,16 @@ __host__ __device__ inline int syn_tailw(int N, int m, int par) {
 // tile), so one A tile serves every instance of the group.  K chunks of 16
 // degrees past the block are skipped.
 // NS stages (a compile-time ring keeps the per-stage index arithmetic of the
-// single-thread producer and MMA issuer cheap); SINGLE: one instance, 16 B rows
-template <int NS, bool SINGLE>
+// single-thread producer and MMA issuer cheap); SINGLE: one instance, 16 B rows.
+//
+// CS > 1 (batches): the CTAs of a cluster take the same items (m, latitude
+// tile) for CS consecutive instance groups (item.z = group / CS).  Each CTA
+// loads a slice of 128 / CS latitudes of every table tile and multicasts it
+// to the whole cluster, so the table crosses from L2 once per cluster
+// instead of once per group; a stage is refilled once the MMAs of every CTA
+// of the cluster are done with it (their commits arrive on each CTA's empty
+// barrier).
+template <int NS, bool SINGLE, int CS = 1>
 __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -594,10 +605,12 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     uint32_t tcols = 32;
     while (tcols < uint32_t(4 * brows)) tcols <<= 1;
+    constexpr uint16_t cmask = uint16_t((1u << CS) - 1u);
+    const int crank = CS > 1 ? int(cluster_ctarank()) : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ns; ++s) {
             mbar_init(&a_full[s], 1);
-            mbar_init(&a_empty[s], 1);
+            mbar_init(&a_empty[s], CS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -611,10 +624,12 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         tmem_relinquish();
     }
     tc_fence_before();
-    __syncthreads();
+    // the cluster's barriers exist before any slice or commit targets them
+    if constexpr (CS > 1) cluster_sync();
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int ib = a.item_off[blockIdx.x], nI = a.item_off[blockIdx.x + 1] - ib;
+    const int ib = a.item_off[blockIdx.x / CS], nI = a.item_off[blockIdx.x / CS + 1] - ib;
     const int N = a.N, nh = a.nh, nlat = a.nlat;
     pdl_launch();
 
@@ -632,7 +647,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
-                const int m = itm.x, mt = itm.y, g = itm.z;
+                const int m = itm.x, mt = itm.y, g = itm.z * CS + crank;
                 for (int par = 0; par < 2; ++par) {
                     const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
                     const int tw = syn_tailw(N, m, par);
@@ -655,8 +670,20 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                         const int w = last ? tw : TC_TILE_K;
                         const int mi = last ? a.nblk + b : b;
                         mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2 + bbytes));
-                        tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
-                        tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        if constexpr (CS == 1) {
+                            tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s],
+                                        pol);
+                            tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s],
+                                        pol);
+                        } else {
+                            // this CTA's slice of latitudes, to every CTA of the cluster
+                            constexpr int rows = TC_TILE_M / CS;
+                            const int off = crank * rows * 128, y = mt * TC_TILE_M + crank * rows;
+                            tma_load_2d_mc(A_hi + s * TC_ATILE + off, &a.map_hi_cs[mi], kt * TC_TILE_K, y, &a_full[s],
+                                           cmask, pol);
+                            tma_load_2d_mc(A_lo + s * TC_ATILE + off, &a.map_lo_cs[mi], kt * TC_TILE_K, y, &a_full[s],
+                                           cmask, pol);
+                        }
                         if (waited) bulk_g2s(Bs + s * bbytes, bsrc + size_t(kt) * bbytes, uint32_t(bbytes), &a_full[s], polb);
                         else pend[s] = bsrc + size_t(kt) * bbytes;
                     }
@@ -697,7 +724,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                                 mma_bf16(d, sdesc_sw128(A_lo + s * TC_ATILE + kk * 32), bd, idesc, 1);
                             }
                         }
-                        mma_commit(&a_empty[s]);
+                        if constexpr (CS > 1) mma_commit_mc(&a_empty[s], cmask);
+                        else mma_commit(&a_empty[s]);
                     }
                 }
                 mma_commit(&acc_full[buf]);
@@ -711,8 +739,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         (void)ld;
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
-            const int m = itm.x, mt = itm.y, g = itm.z, buf = i & 1;
-            const int ngi = SINGLE ? 1 : min(a.ng, a.nb - g * a.ng);
+            const int m = itm.x, mt = itm.y, g = itm.z * CS + crank, buf = i & 1;
+            const int ngi = SINGLE ? 1 : max(0, min(a.ng, a.nb - g * a.ng));
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
             const float mm = float(m);
@@ -777,7 +805,9 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         }
     }
     tc_fence_before();
-    __syncthreads();
+    // no CTA leaves while another of its cluster may still write its shared memory
+    if constexpr (CS > 1) cluster_sync();
+    else __syncthreads();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, tcols);
@@ -1041,10 +1071,48 @@ int launch_analysis_tc(sphnse_plan* P, int nfields) {
 
 // Transposed, padded bf16 hi/lo tables for the synthesis (block (m, parity)
 // stored [nh][pad8(n_par)]) and their tensor maps.
+// Tensor maps of every (m, parity) block of the transposed tables with
+// boxes of `rows` latitudes: entries [0, nblk) box 64 degrees for full K
+// tiles, [nblk, 2 nblk) box syn_tailw for the last K tile (a narrower box
+// keeps the 128-byte row pitch of the swizzled tile, so the MMA descriptors
+// are the same and only the 16-degree chunks it fills are read).
+static int syn_maps(sphnse_plan* P, int rows, void** dhi, void** dlo) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return SPHNSE_E_UNSUPPORTED;
+    const auto& T = P->tc;
+    const int N = P->N, nh = P->nh, nblk = 2 * (N + 1);
+    std::vector<CUtensorMap> mh(2 * nblk), ml(2 * nblk);
+    for (int b = 0; b < nblk; ++b) {
+        const int m = b / 2, par = b % 2;
+        const int np = syn_ndeg(N, m, par);
+        const cuuint64_t dims[2] = {cuuint64_t(np), cuuint64_t(nh)};
+        const cuuint64_t strides[1] = {cuuint64_t(np) * 2};
+        const cuuint32_t es[2] = {1, 1};
+        for (int tail = 0; tail < 2; ++tail) {
+            const cuuint32_t box[2] = {cuuint32_t(tail ? syn_tailw(N, m, par) : TC_TILE_K), cuuint32_t(rows)};
+            for (int l = 0; l < 2; ++l) {
+                __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(l ? T.tsyn_lo : T.tsyn_hi) + T.tsyn_off[b];
+                CUresult r = enc(l ? &ml[tail * nblk + b] : &mh[tail * nblk + b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                 base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
+            }
+        }
+    }
+    if (cudaMalloc(dhi, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess ||
+        cudaMalloc(dlo, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess)
+        return SPHNSE_E_NOMEM;
+    cudaMemcpy(*dhi, mh.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    cudaMemcpy(*dlo, ml.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    return SPHNSE_OK;
+}
+
 int tc_setup_synthesis(sphnse_plan* P) {
     if (P->tc.syn_ready) return SPHNSE_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return SPHNSE_E_UNSUPPORTED;
+    int rc_maps;
     const int N = P->N, nh = P->nh;
     const int nblk = 2 * (N + 1);
     std::vector<size_t> off(nblk + 1, 0);
@@ -1076,34 +1144,8 @@ int tc_setup_synthesis(sphnse_plan* P) {
         return SPHNSE_E_NOMEM;
     cudaMemcpy(T.tsyn_hi, hi.data(), total * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(T.tsyn_lo, lo.data(), total * 2, cudaMemcpyHostToDevice);
-    // per block two maps: box 64 for full K tiles (entries [0, nblk)) and box
-    // syn_tailw for the last K tile (entries [nblk, 2 nblk)); a narrower box
-    // keeps the 128-byte row pitch of the swizzled tile, so the MMA
-    // descriptors are the same and only the 16-degree chunks it fills are read
-    std::vector<CUtensorMap> mh(2 * nblk), ml(2 * nblk);
-    for (int b = 0; b < nblk; ++b) {
-        const int m = b / 2, par = b % 2;
-        const int np = syn_ndeg(N, m, par);
-        const cuuint64_t dims[2] = {cuuint64_t(np), cuuint64_t(nh)};
-        const cuuint64_t strides[1] = {cuuint64_t(np) * 2};
-        const cuuint32_t es[2] = {1, 1};
-        for (int tail = 0; tail < 2; ++tail) {
-            const cuuint32_t box[2] = {cuuint32_t(tail ? syn_tailw(N, m, par) : TC_TILE_K), TC_TILE_M};
-            for (int l = 0; l < 2; ++l) {
-                __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(l ? T.tsyn_lo : T.tsyn_hi) + off[b];
-                CUresult r = enc(l ? &ml[tail * nblk + b] : &mh[tail * nblk + b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                                 base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
-            }
-        }
-    }
-    if (cudaMalloc(&T.smap_hi, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess ||
-        cudaMalloc(&T.smap_lo, 2 * nblk * sizeof(CUtensorMap)) != cudaSuccess)
-        return SPHNSE_E_NOMEM;
-    cudaMemcpy(T.smap_hi, mh.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
-    cudaMemcpy(T.smap_lo, ml.data(), 2 * nblk * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    T.tsyn_off.assign(off.begin(), off.end());
+    if ((rc_maps = syn_maps(P, TC_TILE_M, &T.smap_hi, &T.smap_lo))) return rc_maps;
     // tile list of the B operand: one tile per (m, parity, K tile)
     std::vector<int> toff(nblk + 1, 0);
     for (int b = 0; b < nblk; ++b) toff[b + 1] = toff[b] + syn_nkt(N, b / 2, b % 2);
@@ -1155,34 +1197,50 @@ int tc_setup_synthesis(sphnse_plan* P) {
     return check_cuda(cudaGetLastError());
 }
 
+static int syn_cluster_capacity(int ns, int cs, size_t smem);
+
 // Instance groups of a batch of nb instances of one truncation: ng <= 9
 // instances share every A tile (MMA N = brows = 14 ng rounded up to 16),
 // B tiles [group][tile][brows][64], items (m, latitude tile, group) in LPT
-// order over one CTA per SM.
-int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax) {
-    if (nb < 1 || ngmax < 1 || nsmax < 1) return SPHNSE_E_ARG;
+// order over one CTA per SM.  cs > 1: clusters of cs CTAs take the items
+// of cs consecutive groups together (item.z = group / cs, the group count
+// a multiple of cs) and share every table tile by multicast; the schedule
+// has one bin per cluster that can be resident at once.
+int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax, int cs) {
+    if (nb < 1 || ngmax < 1 || nsmax < 1 || (cs != 1 && cs != 2 && cs != 4)) return SPHNSE_E_ARG;
     const int N = P->N, nh = P->nh;
     TcBatch T;
     T.nb = nb;
+    T.cs = cs;
     // 14 B rows per instance (12 coefficient rows, 2 for u_phi at m = 0); two
     // accumulators of brows <= 128 columns per buffer fit TMEM's 512
     T.ng = std::min(nb, std::min(ngmax, 9));
     T.ngroups = (nb + T.ng - 1) / T.ng;
+    T.ngroups = ((T.ngroups + cs - 1) / cs) * cs;
     T.ng = (nb + T.ngroups - 1) / T.ngroups;   // balanced groups
     T.brows = ((14 * T.ng + 15) / 16) * 16;
     const size_t stage = 2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2;
     T.ns = int(std::min<size_t>(std::min(nsmax, 6), (size_t(227) * 1024 - 1024 - 512) / stage));
+    if (cs > 1) {
+        // slice maps (128 / cs latitudes per box) of this plan, once
+        void** hi = cs == 2 ? &P->tc.smap_hi_c2 : &P->tc.smap_hi_c4;
+        void** lo = cs == 2 ? &P->tc.smap_lo_c2 : &P->tc.smap_lo_c4;
+        if (!*hi) {
+            const int rc = syn_maps(P, TC_TILE_M / cs, hi, lo);
+            if (rc) return rc;
+        }
+    }
     const size_t bytes = size_t(T.ngroups) * P->tc.ntiles * T.brows * TC_TILE_K * 2;
     if (cudaMalloc(reinterpret_cast<void**>(&T.btiles), bytes) != cudaSuccess) return SPHNSE_E_NOMEM;
     cudaMemset(T.btiles, 0, bytes);
     const int nmt = (nh + TC_TILE_M - 1) / TC_TILE_M;
     std::vector<int4> its;
     std::vector<double> cost;
-    for (int g = 0; g < T.ngroups; ++g) {
-        const int ngi = std::min(T.ng, nb - g * T.ng);
+    for (int gq = 0; gq < T.ngroups / cs; ++gq) {
+        const int ngi = std::max(0, std::min(T.ng, nb - gq * cs * T.ng));
         for (int m = 0; m <= N; ++m)
             for (int mt = 0; mt < nmt; ++mt) {
-                its.push_back(make_int4(m, mt, g, 0));
+                its.push_back(make_int4(m, mt, gq, 0));
                 // streamed stages (A and B bytes) plus a fixed cost per item and the epilogue of the group
                 const auto& k0 = P->tc.syn_kt0_host;
                 const int nst = syn_nkt(N, m, 0) - k0[size_t(2 * m) * nmt + mt] + syn_nkt(N, m, 1) -
@@ -1193,7 +1251,16 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax) {
     std::vector<int> order(its.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    const int G = std::min<int>(P->n_cta, int(its.size()));
+    int bins_max = P->n_cta;
+    if (cs > 1) {
+        const size_t sm = 1024 + size_t(T.ns) * (2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2) + 512;
+        bins_max = syn_cluster_capacity(T.ns, cs, sm);
+        if (bins_max < 1) {
+            tc_batch_free(&T);
+            return SPHNSE_E_UNSUPPORTED;
+        }
+    }
+    const int G = std::min<int>(bins_max, int(its.size()));
     std::vector<std::vector<int4>> bins(G);
     std::vector<double> load(G, 0.0);
     for (int idx : order) {
@@ -1214,7 +1281,7 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax) {
     }
     cudaMemcpy(T.items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice);
     cudaMemcpy(T.off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
-    T.ncta = G;
+    T.ncta = G * cs;
     *B = T;
     return check_cuda(cudaGetLastError());
 }
@@ -1235,20 +1302,79 @@ int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha) 
     return check_cuda(e);
 }
 
+typedef void (*SynKernel)(TcSynArgs);
+
+static SynKernel syn_kernel(int ns, bool single, int cs) {
+    if (single) return ns == 6 && cs == 1 ? k_syn_tc<6, true> : nullptr;
+    if (cs == 1) return ns == 6 ? k_syn_tc<6, false> : ns == 5 ? k_syn_tc<5, false> : ns == 4 ? k_syn_tc<4, false>
+                                                                                               : nullptr;
+    if (cs == 2) return ns == 6 ? k_syn_tc<6, false, 2> : ns == 5 ? k_syn_tc<5, false, 2> : ns == 4 ? k_syn_tc<4, false, 2>
+                                                                                                     : nullptr;
+    if (cs == 4) return ns == 6 ? k_syn_tc<6, false, 4> : ns == 5 ? k_syn_tc<5, false, 4> : ns == 4 ? k_syn_tc<4, false, 4>
+                                                                                                     : nullptr;
+    return nullptr;
+}
+
+// Clusters of cs CTAs (smem bytes each) that can be resident at once.
+static int syn_cluster_capacity(int ns, int cs, size_t smem) {
+    SynKernel kern = syn_kernel(ns, false, cs);
+    if (!kern || smem > 227 * 1024) return 0;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs) {
     const size_t sm = 1024 + size_t(B.ns) * (2 * size_t(TC_ATILE) + size_t(B.brows) * TC_TILE_K * 2) + 512;
     if (sm > 227 * 1024 || B.ns > TC_SYN_MAXNS) return SPHNSE_E_UNSUPPORTED;
-    const bool single = B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6;
-    auto kern = single ? k_syn_tc<6, true> : B.ns == 6 ? k_syn_tc<6, false> : B.ns == 5 ? k_syn_tc<5, false>
-                                                                            : k_syn_tc<4, false>;
-    if (!single && (B.ns < 4 || B.ns > 6)) return SPHNSE_E_UNSUPPORTED;
+    const bool single = B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1;
+    SynKernel kern = syn_kernel(B.ns, single, B.cs);
+    if (!kern) return SPHNSE_E_UNSUPPORTED;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    TcSynArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.smap_hi),
-                reinterpret_cast<const CUtensorMap*>(P->tc.smap_lo), B.items, B.off, B.btiles, P->tc.tile_off, gsyn,
+    const auto& T = P->tc;
+    TcSynArgs a{reinterpret_cast<const CUtensorMap*>(T.smap_hi), reinterpret_cast<const CUtensorMap*>(T.smap_lo),
+                B.items, B.off, B.btiles, T.tile_off, gsyn,
                 P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
-                B.ng, B.nb, B.brows, P->tc.ntiles, B.ns, sg_floats / 2, P->tc.syn_kt0, P->tc.syn_nmt};
+                B.ng, B.nb, B.brows, T.ntiles, B.ns, sg_floats / 2, T.syn_kt0, T.syn_nmt,
+                reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_hi_c2 : T.smap_hi_c4),
+                reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_lo_c2 : T.smap_lo_c4)};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
-    const cudaError_t e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
+    cudaError_t e;
+    if (B.cs == 1) {
+        e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
+    } else {
+        prefer_max_smem(reinterpret_cast<const void*>(kern));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(B.ncta);
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = P->stream;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = B.cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        e = cudaLaunchKernelEx(&cfg, kern, a);
+    }
     stage_end(P, SPHNSE_STAGE_SYNTHESIS);
     return check_cuda(e);
 }
@@ -1376,7 +1502,8 @@ int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gan
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
     void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
-                    T.tsyn_lo, T.tile_off, T.tile_info, T.syn_kt0};
+                    T.tsyn_lo, T.tile_off, T.tile_info, T.syn_kt0, T.smap_hi_c2, T.smap_lo_c2, T.smap_hi_c4,
+                    T.smap_lo_c4};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     tc_batch_free(&T.single);

@@ -1,8 +1,7 @@
-// Four-step FP32 longitude transform of the RHS for M = 24 M2 (M2 = 4 .. 64),
-// shared by the ring kernel and the tensor-core synthesis with the ring
-// folded in.  It reads the synthesis output (order-major or
-// latitude-pair-major) and writes the order-major spectra of the analysis
-// directly, without transposes.
+// Four-step FP32 longitude transform of the RHS for M = 24 M2 (M2 = 4 .. 64)
+// as a device function over 128 threads.  It reads the synthesis output
+// (order-major or latitude-pair-major) and writes the order-major spectra of
+// the analysis directly, without transposes.
 //
 // With n = t + M2 n1 and k = k1 + 24 k2 (t, k2 < M2; n1, k1 < 24), and
 // t = b + B a', k2 = c + A d (M2 = A B):
@@ -137,15 +136,30 @@ __device__ __forceinline__ void ring4_rings(const Ring4Args& a, int lat0, int in
     // input gives one float4 per (f, m).  3 (N+1) G / 2 <= 1536 float4 loads
     // per CTA, all of a thread's issued before its stores.
     constexpr int NLD = (3 * 8 * M2 * GP + 127) / 128;
+    // element i = tid + 128 k is (order m, pair-field fr) with i = fr ld + m;
+    // ld = N + 1 is a runtime value, so (m, fr) advance by steps of 128
+    // instead of dividing
+    int m0 = tid, fr0 = 0;
+    while (m0 >= ld) {
+        m0 -= ld;
+        ++fr0;
+    }
     float4 stv[NLD];
+    {
+        int m = m0, fr = fr0;
 #pragma unroll
-    for (int k = 0; k < NLD; ++k) {
-        const int i = tid + 128 * k;
-        const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
-        const int pr = lat0 / 2 + rp;
-        stv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < 3 * ld * GP && 2 * pr < nlat)
-            stv[k] = __ldcg(reinterpret_cast<const float4*>(gs + gsyn_index(a.pairs, f, m, 2 * pr, N, nlat)));
+        for (int k = 0; k < NLD; ++k) {
+            const int rp = fr % GP, f = fr / GP;
+            const int pr = lat0 / 2 + rp;
+            stv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (f < 3 && 2 * pr < nlat)
+                stv[k] = __ldcg(reinterpret_cast<const float4*>(gs + gsyn_index(a.pairs, f, m, 2 * pr, N, nlat)));
+            m += 128;
+            while (m >= ld) {
+                m -= ld;
+                ++fr;
+            }
+        }
     }
     // the previous call's readers of buf and s_rw are done
     sync();
@@ -153,13 +167,20 @@ __device__ __forceinline__ void ring4_rings(const Ring4Args& a, int lat0, int in
     const int lat = lat0 + r;
     const float fc = lat < nlat ? a.two_omega * float(a.x[lat]) : 0.f;
     if (tid < G) s_rw[tid] = lat0 + tid < nlat ? float(a.rw[lat0 + tid]) : 0.f;
+    {
+        int m = m0, fr = fr0;
 #pragma unroll
-    for (int k = 0; k < NLD; ++k) {
-        const int i = tid + 128 * k;
-        if (i < 3 * ld * GP) {
-            const int m = i % ld, fr = i / ld, rp = fr % GP, f = fr / GP;
-            buf[(2 * rp) * RING + f * ld + m] = make_float2(stv[k].x, stv[k].y);
-            buf[(2 * rp + 1) * RING + f * ld + m] = make_float2(stv[k].z, stv[k].w);
+        for (int k = 0; k < NLD; ++k) {
+            const int rp = fr % GP, f = fr / GP;
+            if (f < 3) {
+                buf[(2 * rp) * RING + f * ld + m] = make_float2(stv[k].x, stv[k].y);
+                buf[(2 * rp + 1) * RING + f * ld + m] = make_float2(stv[k].z, stv[k].w);
+            }
+            m += 128;
+            while (m >= ld) {
+                m -= ld;
+                ++fr;
+            }
         }
     }
     sync();

@@ -187,6 +187,29 @@ def test_autotuned_synthesis_shape_gives_the_same_rhs():
     tuned, fixed = out[True][1], out[False][1]
     assert [b["L"] for b in tuned] == [63, 127] and [b["instances"] for b in tuned] == [12, 3]
     for b in tuned:
-        assert 1 <= b["group"] <= 9 and 4 <= b["stages"] <= 6 and b["syn_us"] > 0.0, b
+        assert 1 <= b["group"] <= 9 and 4 <= b["stages"] <= 6 and b["cluster"] in (1, 2, 4) and b["syn_us"] > 0.0, b
     assert [b["group"] for b in fixed] == [6, 3] and all(b["syn_us"] == 0.0 for b in fixed)
     print(tuned)
+
+
+@pytest.mark.parametrize("cluster", [2, 4])
+def test_clustered_synthesis_gives_the_same_rhs(cluster):
+    """CTAs of a cluster sharing every table tile by TMA multicast (each
+    loads a slice of the latitudes for all of them): every instance's F
+    equals the one of the synthesis without clusters, over 3 truncations
+    and group counts that do and do not fill the last cluster."""
+    from paper_1009_3308_gb300 import Ensemble
+    Ls = [63] * 21 + [127] * 5 + [255] * 10
+    nus = [1e-4 * (1 + 0.1 * i) for i in range(len(Ls))]
+    alphas = [coefficients(L, 800 + i, 0.05) * 3 for i, L in enumerate(Ls)]
+    out = {}
+    for cs in (1, cluster):
+        ens = Ensemble(Ls, nus, 1.0, precision="bf16x3", autotune=False, cluster=cs)
+        for i, a in enumerate(alphas):
+            ens.set_alpha(i, _dev(a))
+        for _ in range(2):
+            ens.rhs()
+        out[cs] = [ens.get(i, "F").cpu().numpy() for i in range(len(Ls))]
+        assert [b["cluster"] for b in ens.buckets()] == [cs] * 3
+    for i, (got, ref) in enumerate(zip(out[cluster], out[1])):
+        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref), i
