@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--precision", default=None, help="fp32 | bf16x3 (default: best mixed path)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--only", default=None, choices=sorted(EXTRAS),
+                    help="run this one extra workload alone and print its line (no headline)")
+    ap.add_argument("--ensemble-cluster", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="ensemble BF16X3 synthesis: CTAs per cluster without the autotuner (0: autotuned)")
     return ap.parse_args()
 
 
@@ -456,15 +460,17 @@ def extra_adjoint(torch, nsteps=200, checkpoint=20):
             "grad_norm": float(a0r.grad.norm()), "dJ_dnu": float(nut.grad)}
 
 
-def extra_ensemble(torch, nsteps=200, n=256, precision="fp32"):
+def extra_ensemble(torch, nsteps=200, n=256, precision="fp32", cluster=0):
     """Batched ensemble: 256 instances, L uniform over {63, 127, 255}, nu
     log-uniform in [1e-5, 1e-3], per-instance adaptive steps; "fp32"
     streaming contractions or "bf16x3" (instances of a truncation share every
-    table tile on the tensor cores)."""
+    table tile on the tensor cores; cluster > 0 fixes the CTAs per cluster of
+    the synthesis instead of autotuning its shape)."""
     from paper_1009_3308_gb300 import Ensemble
     from seeded_inputs import ensemble
     mem = ensemble(n)
-    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0, precision=precision)
+    ens = Ensemble([m["L"] for m in mem], [m["nu"] for m in mem], 1.0, precision=precision,
+                   autotune=cluster == 0, cluster=max(cluster, 1))
     for i, m in enumerate(mem):
         ens.set_alpha(i, torch.from_numpy(m["alpha0"]))
     ens.set("RTOL", 1e-6)
@@ -546,10 +552,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# the extra workloads, in the order the full run takes them (prec: the headline's precision)
+EXTRAS = {
+    "ndf_L511": lambda torch, prec, args: extra_ndf_L511(torch, prec),
+    "mixed_errors_L511": lambda torch, prec, args: extra_mixed_errors(torch, prec),
+    "fp64_L255": lambda torch, prec, args: extra_fp64_L255(torch),
+    "coriolis_split_L511": lambda torch, prec, args: extra_coriolis_split(torch, prec),
+    "batched_L511_x4": lambda torch, prec, args: extra_batched_L511(torch),
+    "adjoint_L255": lambda torch, prec, args: extra_adjoint(torch),
+    "ensemble": lambda torch, prec, args: extra_ensemble(torch, nsteps=_ens_steps(args)),
+    "ensemble_bf16x3": lambda torch, prec, args: extra_ensemble(torch, nsteps=_ens_steps(args), precision="bf16x3",
+                                                                cluster=args.ensemble_cluster),
+    "L31_fp64_steps": lambda torch, prec, args: extra_L31(torch),
+    "example2_N100": lambda torch, prec, args: extra_example2(torch),
+}
+
+
+def _ens_steps(args):
+    # the configuration's 200 steps; a shorter run with --only and --steps (profiling targets)
+    return min(args.steps, 200) if args.only else 200
+
+
+def run_only(args):
+    """One extra workload alone (one GPU), e.g. as a profiling target."""
+    import torch
+    prec = args.precision or _best_mixed()
+    out = EXTRAS[args.only](torch, prec, args)
+    print(json.dumps({"workload": args.only, **out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only:
+        run_only(args)
         return
     import numpy as np
     import torch
@@ -679,18 +717,9 @@ def main():
         extras["rel_err_vs_fp64"] = float(np.linalg.norm(fm - f64) / np.linalg.norm(f64))
         if "fp64" in extras:
             extras["speedup_vs_fp64"] = value / world / extras["fp64"]["rhs_per_s"]
-        for name, fn in (("ndf_L511", lambda: extra_ndf_L511(torch, prec)),
-                         ("mixed_errors_L511", lambda: extra_mixed_errors(torch, prec)),
-                         ("fp64_L255", lambda: extra_fp64_L255(torch)),
-                         ("coriolis_split_L511", lambda: extra_coriolis_split(torch, prec)),
-                         ("batched_L511_x4", lambda: extra_batched_L511(torch)),
-                         ("adjoint_L255", lambda: extra_adjoint(torch)),
-                         ("ensemble", lambda: extra_ensemble(torch)),
-                         ("ensemble_bf16x3", lambda: extra_ensemble(torch, precision="bf16x3")),
-                         ("L31_fp64_steps", lambda: extra_L31(torch)),
-                         ("example2_N100", lambda: extra_example2(torch))):
+        for name, fn in EXTRAS.items():
             try:
-                extras[name] = fn()
+                extras[name] = fn(torch, prec, args)
             except Exception as e:  # an extra must not hide the headline line
                 extras[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
 

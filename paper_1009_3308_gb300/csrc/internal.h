@@ -346,6 +346,13 @@ int check_cuda(cudaError_t e);
 // which defeats the early launch below.
 void prefer_max_smem(const void* kernel);
 
+// Raise the kernel's dynamic shared-memory cap to at least `bytes` and never
+// lower it.  One kernel is launched with different sizes by different
+// plans, ensemble buckets and tuned shapes, and launches recorded in graphs
+// are checked against the cap as it stands when they run (a profiler
+// replays graph nodes one by one): the cap must cover every size ever used.
+void allow_dynamic_smem(const void* kernel, size_t bytes);
+
 // Launch with programmatic stream serialisation (the kernel calls pdl_wait()
 // before it reads what its predecessor on the stream wrote).
 template <typename... KArgs, typename... Args>

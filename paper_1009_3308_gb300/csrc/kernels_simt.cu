@@ -370,7 +370,7 @@ static int synth_t(sphnse_plan* P, int pairs) {
     dim3 blk(128), grd((P->nh + 127) / 128, P->N + 1);
     size_t sm = size_t(P->N + 2) * 2 * NF * sizeof(T);
     if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_synthesis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        allow_dynamic_smem(reinterpret_cast<const void*>(k_synthesis<T, NF>), sm);
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     launch_pdl_small(P->n_cta, k_synthesis<T, NF>, grd, blk, sm, P->stream,
                reinterpret_cast<const T*>(P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn),
@@ -395,7 +395,7 @@ static int anal_t(sphnse_plan* P) {
     dim3 blk(128), grd((maxrows + 127) / 128, P->N + 1, 2);
     size_t sm = size_t(P->nh) * 2 * NF * sizeof(T);
     if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_analysis<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        allow_dynamic_smem(reinterpret_cast<const void*>(k_analysis<T, NF>), sm);
     }
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     launch_pdl_small(P->n_cta, k_analysis<T, NF>, grd, blk, sm, P->stream,

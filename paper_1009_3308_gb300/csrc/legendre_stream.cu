@@ -382,7 +382,7 @@ static int syn_stream_t(sphnse_plan* P, int pairs) {
     const size_t sm = 128 + sizeof(T) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * (P->N + 2) * 2 * NF +
                                          size_t(P->nh) * 2 * NF);
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_syn_stream<T, NF, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_syn_stream<T, NF, HR>), sm);
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, P->d_bsyn, P->d_gsyn, nullptr, nullptr,
                  P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0, pairs};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
@@ -400,7 +400,7 @@ static int ana_stream_t(sphnse_plan* P) {
     constexpr int NST = nst<T>();
     const size_t sm = 128 + sizeof(T) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * 2 * P->nh * 2 * NF);
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_ana_stream<T, NF, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_stream<T, NF, HR, NTEAM>), sm);
     StreamArgs a{P->tab[sizeof(T) == 8 ? SPHNSE_FP64 : SPHNSE_FP32].syn, nullptr, nullptr, P->d_gana, P->d_hana,
                  P->d_s, P->d_items, P->d_item_off, P->d_status, P->N, P->nh, P->nlat, 0, 0, 0, 0, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
@@ -430,7 +430,7 @@ int launch_synthesis_stream_batch(sphnse_plan* P, const int* items, const int* i
     const size_t sm = 128 + sizeof(float) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * (P->N + 2) * 6 +
                                              size_t(P->nh) * 6);
     if (threads > 512 || sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_syn_stream<float, 3, HR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_syn_stream<float, 3, HR>), sm);
     StreamArgs a{P->tab[SPHNSE_FP32].syn, bsyn, gsyn, nullptr, nullptr, P->d_s, items, item_off, P->d_status,
                  P->N, P->nh, P->nlat, sb, sg, 0, 0, pairs};
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
@@ -448,7 +448,7 @@ int launch_analysis_stream_batch(sphnse_plan* P, const int* items, const int* it
     const int threads = 32 + 32 * QPS * NTEAM;
     const size_t sm = 128 + sizeof(float) * (size_t(NST) * 2 * HR * P->nh + size_t(2) * 2 * P->nh * 4);
     if (sm > 227 * 1024 || !stream_ok(P, SPHNSE_FP32)) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_ana_stream<float, 2, HR, NTEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_stream<float, 2, HR, NTEAM>), sm);
     StreamArgs a{P->tab[SPHNSE_FP32].syn, nullptr, nullptr, gana, hana, P->d_s, items, item_off, P->d_status,
                  P->N, P->nh, P->nlat, 0, 0, sa, sh, 0};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);

@@ -1052,7 +1052,7 @@ static int ana_tc_t(sphnse_plan* P) {
     const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
     const size_t sm = 1024 + 2 * size_t(TC_ANA_NS) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256;
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(k_ana_tc<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_tc<NF>), sm);
     TcAnaArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi), reinterpret_cast<const CUtensorMap*>(P->tc.map_lo),
                 P->tc.ana_items, P->tc.ana_off, P->tc.ana_pieces,
                 reinterpret_cast<const float*>(P->d_gana), reinterpret_cast<float*>(P->d_hana), P->d_status,
@@ -1319,7 +1319,7 @@ static SynKernel syn_kernel(int ns, bool single, int cs) {
 static int syn_cluster_capacity(int ns, int cs, size_t smem) {
     SynKernel kern = syn_kernel(ns, false, cs);
     if (!kern || smem > 227 * 1024) return 0;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    allow_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(192);
@@ -1345,7 +1345,7 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     const bool single = B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1;
     SynKernel kern = syn_kernel(B.ns, single, B.cs);
     if (!kern) return SPHNSE_E_UNSUPPORTED;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(kern), sm);
     const auto& T = P->tc;
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(T.smap_hi), reinterpret_cast<const CUtensorMap*>(T.smap_lo),
                 B.items, B.off, B.btiles, T.tile_off, gsyn,
@@ -1489,7 +1489,7 @@ int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gan
     cudaError_t e = launch_pdl(k_ana_prep, dim3(((P->N + 1) * B.nkt * 16 + 127) / 128, B.nb), dim3(128), 0, P->stream, gana,
                                sa_floats, B.stiles, P->N, P->nh, P->nlat, B.nkt);
     if (e == cudaSuccess) {
-        cudaFuncSetAttribute(k_ana_tc_b, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_tc_b), sm);
         TcAnaBArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.map_hi),
                      reinterpret_cast<const CUtensorMap*>(P->tc.map_lo), B.items, B.off, B.slots, B.stiles, hana,
                      sh_floats, P->d_status, P->N, B.nkt, P->n_ext};

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <unordered_map>
 #include <unordered_set>
 
 #include <cmath>
@@ -121,6 +122,16 @@ int ensure_tables(sphnse_plan* P, int prec) {
     }
     t.built = true;
     return SPHNSE_OK;
+}
+
+void allow_dynamic_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> cap;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& c = cap[kernel];
+    if (bytes > c && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) ==
+                         cudaSuccess)
+        c = bytes;
 }
 
 void prefer_max_smem(const void* kernel) {

@@ -214,7 +214,7 @@ template <typename T, typename TW, int MODE>
 static void ring_t(sphnse_plan* P, const RingArgs& a, const TW* tw, int threads, int nb = 1) {
     const int nbuf = MODE == RING_ADJOINT ? 3 : (MODE == RING_PROJECT ? 1 : 2);
     const size_t sm = size_t(nbuf) * P->nlon * sizeof(cx<T>) + size_t(P->nlon) * 2 * sizeof(T);
-    cudaFuncSetAttribute(k_ring<T, TW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ring<T, TW, MODE>), sm);
     launch_pdl_small(P->n_cta, k_ring<T, TW, MODE>, dim3(P->nlat, nb), dim3(threads), sm, P->stream, a, P->fft, tw);
 }
 
@@ -296,7 +296,7 @@ template <int M2>
 static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga, int pairs) {
     constexpr size_t sm = ring4_smem<M2>();
     static_assert(sm <= 227 * 1024, "ring4 shared memory");
-    cudaFuncSetAttribute(k_ring4<M2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ring4<M2>), sm);
     Ring4Args a;
     a.N = P->N;
     a.nlat = P->nlat;
