@@ -25,12 +25,17 @@
 
 namespace sph {
 
+// Padded strides of the shared-memory tiles (found with a bank model of the
+// 64-bit accesses of every pass) and the ring buffer length.  SW: pass 2b
+// maps thread t to (c, kq2) = (t / B, t % B) instead of (t % A, t / A);
+// at M2 = 32 that keeps the one two-way conflicted pass of the unpadded
+// element stride in 864 instead of 960 entries, so four CTAs fit an SM.
 template <int M2> struct R4;
-template <> struct R4<64> { static constexpr int A = 8, P1 = 72, Bp = 9, Q = 72, RING = 1728; };
-template <> struct R4<32> { static constexpr int A = 8, P1 = 36, Bp = 5, Q = 40, RING = 960; };
-template <> struct R4<16> { static constexpr int A = 4, P1 = 20, Bp = 5, Q = 20, RING = 480; };
-template <> struct R4<8> { static constexpr int A = 8, P1 = 9, Bp = 1, Q = 9, RING = 216; };
-template <> struct R4<4> { static constexpr int A = 4, P1 = 5, Bp = 1, Q = 5, RING = 124; };
+template <> struct R4<64> { static constexpr int A = 8, P1 = 72, Bp = 9, Q = 72, RING = 1728; static constexpr bool SW = false; };
+template <> struct R4<32> { static constexpr int A = 8, P1 = 36, Bp = 4, Q = 35, RING = 864; static constexpr bool SW = true; };
+template <> struct R4<16> { static constexpr int A = 4, P1 = 20, Bp = 5, Q = 20, RING = 480; static constexpr bool SW = false; };
+template <> struct R4<8> { static constexpr int A = 8, P1 = 9, Bp = 1, Q = 9, RING = 216; static constexpr bool SW = false; };
+template <> struct R4<4> { static constexpr int A = 4, P1 = 5, Bp = 1, Q = 5, RING = 124; static constexpr bool SW = false; };
 
 // cos, sin of 2 pi j / 24, j = 0..14
 __device__ constexpr double kC24[15] = {1.0, 0.96592582628906828675, 0.86602540378443864676, 0.7071067811865475244,
@@ -267,7 +272,7 @@ __device__ __forceinline__ void ring4_rings(const Ring4Args& a, int lat0, int in
         }
         sync();
         // pass 2b: task (k1 = j B + kq2, c) -> X[k1 + 24 (c + A d)]
-        const int c = t % A, kq2 = t / A;
+        const int c = C::SW ? t / B : t % A, kq2 = C::SW ? t % B : t / A;
         cx<float> va[TB][B], vb[TB][B];
 #pragma unroll
         for (int j = 0; j < TB; ++j) {
