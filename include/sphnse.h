@@ -468,9 +468,10 @@ int sphnse_stage_times(sphnse_plan* plan, double* ms, long* launches);
  * library, held until the process exits).  Sizes with n > 2048 *
  * SPHNSE_NOALLOC_MAX_BLOCKS (L above about 4090) return SPHNSE_E_TOO_LARGE.
  * The first call on a device looks up the array's device address with that
- * device current (a one-time set-up); make that first call before any
- * stream capture.  All calls share the array and each call overwrites the
- * slots it reads; calls that overlap on the GPU race on it. */
+ * device current (a one-time set-up; a lookup that fails returns
+ * SPHNSE_E_CUDA and is tried again by the next call); make that first call
+ * before any stream capture.  All calls share the array and each call
+ * overwrites the slots it reads; calls that overlap on the GPU race on it. */
 #define SPHNSE_NOALLOC_MAX_BLOCKS 4096
 int sphnse_nu_sensitivity_noalloc(int L, const double* alpha, const double* w, double* out, void* stream);
 

@@ -15,6 +15,7 @@
 // overlap on the GPU (different streams, or host threads) race on it.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "internal.h"
@@ -28,12 +29,22 @@ constexpr int NA_THREADS = 256;
 constexpr int NA_PER_THREAD = 8;
 constexpr int NA_PER_BLOCK = NA_THREADS * NA_PER_THREAD;
 
-// device address of g_noalloc_partial, looked up once per device with that
-// device current (in host code the symbol names a host-side stand-in)
+// device address of g_noalloc_partial per device, looked up with that device
+// current (in host code the symbol names a host-side stand-in); only a
+// successful lookup is kept, so a failed one is tried again on the next call
 constexpr int NA_MAX_DEVICES = 64;
-std::once_flag g_once[NA_MAX_DEVICES];
-double* g_addr[NA_MAX_DEVICES];
-cudaError_t g_err[NA_MAX_DEVICES];
+std::mutex g_lookup;
+std::atomic<double*> g_addr[NA_MAX_DEVICES];
+
+double* scratch_address(int dev) {
+    double* p = g_addr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    std::lock_guard<std::mutex> lk(g_lookup);
+    p = g_addr[dev].load(std::memory_order_relaxed);
+    if (!p && cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_partial) == cudaSuccess && p)
+        g_addr[dev].store(p, std::memory_order_release);
+    return g_addr[dev].load(std::memory_order_relaxed);
+}
 
 // packed index i -> degree L (m-major order, L = max(m,1)..N)
 __device__ __forceinline__ int degree_of(int N, int i) {
@@ -95,14 +106,12 @@ extern "C" int sphnse_nu_sensitivity_noalloc(int L, const double* alpha, const d
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SPHNSE_E_CUDA;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return SPHNSE_E_UNSUPPORTED;
-    std::call_once(g_once[dev], [dev]() {
-        g_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_addr[dev]), g_noalloc_partial);
-    });
-    if (g_err[dev] != cudaSuccess || !g_addr[dev]) return SPHNSE_E_CUDA;
+    double* part = scratch_address(dev);
+    if (!part) return SPHNSE_E_CUDA;
     const int nb = int((n + NA_PER_BLOCK - 1) / NA_PER_BLOCK);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     k_na_partial<<<nb, NA_THREADS, 0, s>>>(reinterpret_cast<const double2*>(alpha),
-                                           reinterpret_cast<const double2*>(w), L, int(n), g_addr[dev]);
-    k_na_final<<<1, NA_THREADS, 0, s>>>(g_addr[dev], nb, out);
+                                           reinterpret_cast<const double2*>(w), L, int(n), part);
+    k_na_final<<<1, NA_THREADS, 0, s>>>(part, nb, out);
     return cudaGetLastError() == cudaSuccess ? SPHNSE_OK : SPHNSE_E_CUDA;
 }
