@@ -78,6 +78,12 @@ extern "C" {
                                         * group, pipeline stages, CTAs per cluster) when BF16X3
                                         * is selected and keeps the fastest (sphnse_ensemble_bucket);
                                         * 0 takes the widest instance groups; set it first */
+#define SPHNSE_KEY_RING_THREADS   13  /* four-step FFT ring kernel (nlon = 24 M2): threads per
+                                         CTA of 128 / M2 latitude rings.  128: one thread per
+                                         column carries both packed spectra; 256 (M2 >= 16):
+                                         a thread per column and spectrum, for grids of less
+                                         than four CTAs per SM; 0 (default) chooses by the
+                                         grid.  The results are identical */
 #define SPHNSE_KEY_SYN_CLUSTER    14  /* ensemble, with SPHNSE_KEY_AUTOTUNE 0: CTAs per cluster of
                                          the batched tensor-core synthesis (1 default, 2, 4); the
                                          CTAs of a cluster take consecutive instance groups and

@@ -16,7 +16,8 @@ E_CODES = {-1: "E_ARG", -2: "E_INEXACT", -3: "E_NOMEM", -4: "E_CUDA", -5: "E_NON
            -6: "E_STEP_TOO_SMALL", -7: "E_TIMEOUT", -8: "E_UNSUPPORTED", -9: "E_TOO_LARGE"}
 KEY = dict(PRECISION=1, NU=2, OMEGA=3, RTOL=4, ATOL=5, MAX_ORDER=6, NEWTON_MAX_ITER=7,
            H_MAX=8, BDF=9, CORIOLIS_SPLIT=10, TIMING_PERIOD=11, N_COEFF=100, L=101, NLAT=102, NLON=103, TABLE_BYTES=104, ROUNDS=105,
-           SYN_ENTRIES=106, ANA_ENTRIES=107, AUTOTUNE=12, BUCKETS=108, SYN_CLUSTER=14)
+           SYN_ENTRIES=106, ANA_ENTRIES=107, AUTOTUNE=12, BUCKETS=108, SYN_CLUSTER=14,
+           RING_THREADS=13)
 PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2}
 MAXK = 5
 STAGES = ("prep", "synthesis", "ring", "analysis", "finish", "step", "transpose")

@@ -250,6 +250,8 @@ struct sphnse_plan {
     // optional per-stage CUDA-event timing on the plan's stream
     unsigned timing = 0;         // bit mask of timed stages
     int timing_period = 1;       // record every timing_period-th launch of a timed stage
+    int ring_threads = 0;        // four-step ring kernel: 0 chooses, 128 or 256 threads per G rings
+    int nsm = 1;                 // SMs of the plan's device
     long stage_calls[8] = {};    // launches seen per stage while timed
     bool stage_rec[8] = {};      // the current launch of the stage is recorded
     std::vector<cudaEvent_t> ev[SPHNSE_NSTAGES];

@@ -370,6 +370,7 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device);
         if (nsm < 1) nsm = 1;
+        P->nsm = nsm;
         const int G = nsm < L + 1 ? nsm : L + 1;
         std::vector<std::vector<int>> bins(G);
         std::vector<long> load(G, 0);
@@ -432,6 +433,7 @@ int sphnse_plan_set(sphnse_plan* P, int key, double v) {
         case SPHNSE_KEY_BDF: P->bdf = v != 0.0; return SPHNSE_OK;
         case SPHNSE_KEY_CORIOLIS_SPLIT: P->coriolis_split = v != 0.0; return SPHNSE_OK;
         case SPHNSE_KEY_TIMING_PERIOD: if (v < 1 || v > 1e6) return SPHNSE_E_ARG; P->timing_period = int(v); return SPHNSE_OK;
+        case SPHNSE_KEY_RING_THREADS: if (v != 0 && v != 128 && v != 256) return SPHNSE_E_ARG; P->ring_threads = int(v); return SPHNSE_OK;
         default: return SPHNSE_E_ARG;
     }
 }
@@ -450,6 +452,7 @@ int sphnse_plan_get(const sphnse_plan* P, int key, double* v) {
         case SPHNSE_KEY_BDF: *v = P->bdf; break;
         case SPHNSE_KEY_CORIOLIS_SPLIT: *v = P->coriolis_split; break;
         case SPHNSE_KEY_TIMING_PERIOD: *v = P->timing_period; break;
+        case SPHNSE_KEY_RING_THREADS: *v = P->ring_threads; break;
         case SPHNSE_KEY_N_COEFF: *v = P->n_coeff; break;
         case SPHNSE_KEY_L: *v = P->N; break;
         case SPHNSE_KEY_NLAT: *v = P->nlat; break;

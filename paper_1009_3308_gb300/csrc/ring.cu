@@ -292,6 +292,16 @@ __global__ void __launch_bounds__(128, 4) k_ring4(Ring4Args a) {
     ring4_rings<M2>(a, blockIdx.x * (128 / M2), blockIdx.y, threadIdx.x, sm4, s_rw, [] { __syncthreads(); });
 }
 
+// 256 threads per G = 128 / M2 rings (grids of less than a wave)
+template <int M2>
+__global__ void __launch_bounds__(256, 3) k_ring4w(Ring4Args a) {
+    extern __shared__ __align__(16) float2 sm4[];
+    __shared__ float s_rw[128 / M2];
+    pdl_launch();
+    pdl_wait();
+    ring4w_rings<M2>(a, blockIdx.x * (128 / M2), blockIdx.y, threadIdx.x, sm4, s_rw, [] { __syncthreads(); });
+}
+
 template <int M2>
 static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float* gana, size_t sga, int pairs) {
     constexpr size_t sm = ring4_smem<M2>();
@@ -310,7 +320,18 @@ static int ring4_t(sphnse_plan* P, int nb, const float* gsyn, size_t sgs, float*
     a.sga = sga / 2;
     a.pairs = pairs;
     constexpr int G = 128 / M2;
-    return check_cuda(launch_pdl(k_ring4<M2>, dim3((P->nlat + G - 1) / G, nb), dim3(128), sm, P->stream, a));
+    const dim3 grid((P->nlat + G - 1) / G, nb);
+    if constexpr (M2 >= 16) {
+        // a grid of less than four CTAs per SM is latency-bound: twice the
+        // threads per ring shorten each thread's chain of passes
+        const bool wide = P->ring_threads == 256 ||
+                          (P->ring_threads == 0 && size_t(grid.x) * grid.y <= size_t(4) * P->nsm);
+        if (wide) {
+            allow_dynamic_smem(reinterpret_cast<const void*>(k_ring4w<M2>), sm);
+            return check_cuda(launch_pdl(k_ring4w<M2>, grid, dim3(256), sm, P->stream, a));
+        }
+    }
+    return check_cuda(launch_pdl(k_ring4<M2>, grid, dim3(128), sm, P->stream, a));
 }
 
 int ring4_m2(int nlon, int nlat) {

@@ -259,6 +259,9 @@ __device__ __forceinline__ void ring4_rings(const Ring4Args& a, int lat0, int in
         za = {-q * zb.x, q * za.y};
     };
 
+    // From pass 2b on, the B buffers are free once the B values are in
+    // registers: the remaining passes alternate between XA and XB, so each
+    // needs one barrier.
     if constexpr (B > 1) {
         sync();
 #pragma unroll
@@ -271,76 +274,296 @@ __device__ __forceinline__ void ring4_rings(const Ring4Args& a, int lat0, int in
             }
         }
         sync();
-        // pass 2b: task (k1 = j B + kq2, c) -> X[k1 + 24 (c + A d)]
+        // pass 2b: task (k1 = j B + kq2, c) -> X[k1 + 24 (c + A d)]; every
+        // task stores W back where it read A
         const int c = C::SW ? t / B : t % A, kq2 = C::SW ? t % B : t / A;
-        cx<float> va[TB][B], vb[TB][B];
 #pragma unroll
         for (int j = 0; j < TB; ++j) {
             const int k1 = j * B + kq2;
+            cx<float> va[B], vb[B];
 #pragma unroll
             for (int bb = 0; bb < B; ++bb) {
-                va[j][bb] = ld2(&XA[k1 * Q + c * Bp + bb]);
-                vb[j][bb] = ld2(&XB[k1 * Q + c * Bp + bb]);
+                va[bb] = ld2(&XA[k1 * Q + c * Bp + bb]);
+                vb[bb] = ld2(&XB[k1 * Q + c * Bp + bb]);
             }
-            dftn<B>(va[j], +1);
-            dftn<B>(vb[j], +1);
+            dftn<B>(va, +1);
+            dftn<B>(vb, +1);
 #pragma unroll
-            for (int d = 0; d < B; ++d) product(va[j][d], vb[j][d]);
+            for (int d = 0; d < B; ++d) product(va[d], vb[d]);
             // forward, backwards through the factorisation: B-point DFT over d
-            dftn<B>(va[j], -1);
+            dftn<B>(va, -1);
 #pragma unroll
-            for (int bb = 1; bb < B; ++bb) va[j][bb] = cmul(va[j][bb], conjg2(&tw2[c * B2 + bb]));
+            for (int bb = 1; bb < B; ++bb) va[bb] = cmul(va[bb], conjg2(&tw2[c * B2 + bb]));
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb) st2(&XA[k1 * Q + c * Bp + bb], va[bb]);
         }
         sync();
+        // A-point DFT over c -> a', twiddle e^{-2 pi i t k1 / M} with t = b + B a'
 #pragma unroll
-        for (int j = 0; j < TB; ++j) {
-            const int k1 = j * B + kq2;
+        for (int j = 0; j < TA; ++j) {
+            const int k1 = j * A + kq;
+            cx<float> y[A];
 #pragma unroll
-            for (int bb = 0; bb < B; ++bb) st2(&XA[k1 * Q + c * Bp + bb], va[j][bb]);
+            for (int cc = 0; cc < A; ++cc) y[cc] = ld2(&XA[k1 * Q + cc * Bp + b]);
+            dftn<A>(y, -1);
+#pragma unroll
+            for (int ap = 0; ap < A; ++ap) st2(&XB[k1 * P1 + b + B * ap], cmul(y[ap], conjg2(&tw1[k1 * P1 + b + B * ap])));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < TA; ++j) {
+            const int k1 = j * A + kq;
+#pragma unroll
+            for (int cc = 0; cc < A; ++cc) product(ua[j][cc], ub[j][cc]);
+            dftn<A>(ua[j], -1);
+#pragma unroll
+            for (int ap = 0; ap < A; ++ap) ua[j][ap] = cmul(ua[j][ap], conjg2(&tw1[k1 * P1 + b + B * ap]));
         }
         sync();
 #pragma unroll
         for (int j = 0; j < TA; ++j) {
             const int k1 = j * A + kq;
 #pragma unroll
-            for (int cc = 0; cc < A; ++cc) ua[j][cc] = ld2(&XA[k1 * Q + cc * Bp + b]);
+            for (int ap = 0; ap < A; ++ap) st2(&XB[k1 * P1 + b + B * ap], ua[j][ap]);
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < TA; ++j)
-#pragma unroll
-            for (int cc = 0; cc < A; ++cc) product(ua[j][cc], ub[j][cc]);
-    }
-    // A-point DFT over c -> a', twiddle e^{-2 pi i t k1 / M} with t = b + B a'
-#pragma unroll
-    for (int j = 0; j < TA; ++j) {
-        const int k1 = j * A + kq;
-        dftn<A>(ua[j], -1);
-#pragma unroll
-        for (int ap = 0; ap < A; ++ap) ua[j][ap] = cmul(ua[j][ap], conjg2(&tw1[k1 * P1 + b + B * ap]));
     }
     sync();
+    // 24-point DFT over k1 -> W's spectrum at n = t + M2 n1; only m <= N and
+    // m >= M - N are read back: n1 = 8 .. 15 are never needed
+    {
+        cx<float> y[24];
 #pragma unroll
-    for (int j = 0; j < TA; ++j) {
-        const int k1 = j * A + kq;
+        for (int k1 = 0; k1 < 24; ++k1) y[k1] = ld2(&XB[k1 * P1 + t]);
+        dft24<-1>(y);
 #pragma unroll
-        for (int ap = 0; ap < A; ++ap) st2(&XA[k1 * P1 + b + B * ap], ua[j][ap]);
+        for (int n1 = 0; n1 < 24; ++n1)
+            if (n1 < 8 || n1 >= 16) st2(&XA[t + M2 * n1], y[n1]);
     }
-    sync();
-    // 24-point DFT over k1 -> W's spectrum at n = t + M2 n1
-    cx<float> y[24];
-#pragma unroll
-    for (int k1 = 0; k1 < 24; ++k1) y[k1] = ld2(&XA[k1 * P1 + t]);
-    dft24<-1>(y);
-    sync();
-    // only m <= N and m >= M - N are read back: n1 = 8 .. 15 are never needed
-#pragma unroll
-    for (int n1 = 0; n1 < 24; ++n1)
-        if (n1 < 8 || n1 >= 16) st2(&XA[t + M2 * n1], y[n1]);
     sync();
 
     // separate the two real fields, truncate to m <= N, weight, store
     for (int i = tid; i < ld * GP; i += 128) {
+        const int rp = i % GP, m = i / GP;
+        const int l = lat0 + 2 * rp;
+        if (l >= nlat) continue;
+        float4 oA, oB;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float2* Z = buf + (2 * rp + e) * RING;
+            const float2 p = Z[m], q = Z[(M - m) % M];
+            const float sc = s_rw[2 * rp + e];
+            const float ax = 0.5f * (p.x + q.x) * sc, ay = 0.5f * (p.y - q.y) * sc;
+            const float bx = 0.5f * (p.y + q.y) * sc, by = 0.5f * (q.x - p.x) * sc;
+            if (e == 0) {
+                oA.x = ax; oA.y = ay; oB.x = bx; oB.y = by;
+            } else {
+                oA.z = ax; oA.w = ay; oB.z = bx; oB.w = by;
+            }
+        }
+        *reinterpret_cast<float4*>(ga + size_t(m) * nlat + l) = oA;
+        *reinterpret_cast<float4*>(ga + size_t(ld + m) * nlat + l) = oB;
+    }
+}
+
+
+// The same transform of G = 128 / M2 rings by 256 threads (B > 1, i.e.
+// M2 >= 16), for grids too small to fill the GPU: thread tid = 128 h + M2 r
+// + t carries one signal of ring r through the inverse passes, A (h = 0) or
+// B (h = 1), so each thread's chain holds one 24-point and three A- and
+// three B-point DFTs fewer.  In pass 2b the B threads leave their values in
+// place in shared memory for the A threads, which take the product and the
+// forward transform alone.  Every signal sees the same operations in the
+// same order as in ring4_rings, so the results are identical.
+template <int M2, typename Sync>
+__device__ __forceinline__ void ring4w_rings(const Ring4Args& a, int lat0, int inst, int tid, float2* sm, float* s_rw,
+                                             Sync sync) {
+    using C = R4<M2>;
+    constexpr int M = 24 * M2, A = C::A, B = M2 / A, P1 = C::P1, Bp = C::Bp, Q = C::Q, RING = C::RING;
+    constexpr int G = 128 / M2, GP = G / 2, B2 = B + 1;
+    constexpr int TA = 24 / A, TB = 24 / B;
+    constexpr int NT = 256;
+    static_assert(B > 1, "the wide ring transform exchanges pass-2b tiles");
+    const float2* __restrict__ tw1 = a.ftw;
+    const float2* __restrict__ tw2 = tw1 + 24 * P1;
+    float2* buf = sm;
+    const int N = a.N, nlat = a.nlat, ld = N + 1;
+    const float2* gs = a.gsyn + size_t(inst) * a.sgs;
+    float2* ga = a.gana + size_t(inst) * a.sga;
+
+    // stage the spectra as in ring4_rings, 256 threads
+    constexpr int NLD = (3 * 8 * M2 * GP + NT - 1) / NT;
+    int m0 = tid, fr0 = 0;
+    while (m0 >= ld) {
+        m0 -= ld;
+        ++fr0;
+    }
+    float4 stv[NLD];
+    {
+        int m = m0, fr = fr0;
+#pragma unroll
+        for (int k = 0; k < NLD; ++k) {
+            const int rp = fr % GP, f = fr / GP;
+            const int pr = lat0 / 2 + rp;
+            stv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (f < 3 && 2 * pr < nlat)
+                stv[k] = __ldcg(reinterpret_cast<const float4*>(gs + gsyn_index(a.pairs, f, m, 2 * pr, N, nlat)));
+            m += NT;
+            while (m >= ld) {
+                m -= ld;
+                ++fr;
+            }
+        }
+    }
+    sync();
+    const int h = tid / 128, u = tid % 128, r = u / M2, t = u % M2;
+    const int lat = lat0 + r;
+    const float fc = lat < nlat ? a.two_omega * float(a.x[lat]) : 0.f;
+    if (tid < G) s_rw[tid] = lat0 + tid < nlat ? float(a.rw[lat0 + tid]) : 0.f;
+    {
+        int m = m0, fr = fr0;
+#pragma unroll
+        for (int k = 0; k < NLD; ++k) {
+            const int rp = fr % GP, f = fr / GP;
+            if (f < 3) {
+                buf[(2 * rp) * RING + f * ld + m] = make_float2(stv[k].x, stv[k].y);
+                buf[(2 * rp + 1) * RING + f * ld + m] = make_float2(stv[k].z, stv[k].w);
+            }
+            m += NT;
+            while (m >= ld) {
+                m -= ld;
+                ++fr;
+            }
+        }
+    }
+    sync();
+    float2* XA = buf + r * RING;
+    float2* XB = buf + (G + r) * RING;
+    float2* X = h ? XB : XA;
+
+    // pass 1: A = zeta + i u_theta (h = 0) or B = u_phi (h = 1)
+    cx<float> x[24];
+#pragma unroll
+    for (int n1 = 0; n1 < 24; ++n1) {
+        const int n = t + M2 * n1;
+        cx<float> z{0.f, 0.f};
+        if (n1 >= 8 && n1 < 16) {
+        } else if (n <= N) {
+            if (h == 0) {
+                float2 g0 = XA[n], g1 = XA[ld + n];
+                if (n == 0) g0.y = g1.y = 0.f;
+                z = {g0.x - g1.y, g0.y + g1.x};
+            } else {
+                const float2 g2 = XA[2 * ld + n];
+                z = {g2.x, n == 0 ? 0.f : g2.y};
+            }
+        } else if (n >= M - N) {
+            const int mm = M - n;
+            if (h == 0) {
+                const float2 g0 = XA[mm], g1 = XA[ld + mm];
+                z = {g0.x + g1.y, g1.x - g0.y};
+            } else {
+                const float2 g2 = XA[2 * ld + mm];
+                z = {g2.x, -g2.y};
+            }
+        }
+        x[n1] = z;
+    }
+    dft24<+1>(x);
+#pragma unroll
+    for (int k1 = 1; k1 < 24; ++k1) x[k1] = cmul(x[k1], ldg2(&tw1[k1 * P1 + t]));
+    sync();
+#pragma unroll
+    for (int k1 = 0; k1 < 24; ++k1) st2(&X[k1 * P1 + t], x[k1]);
+    sync();
+
+    // pass 2a: task (k1 = j A + kq, b) of this thread's signal
+    const int b = t % B, kq = t / B;
+    {
+    cx<float> uu[TA][A];
+#pragma unroll
+    for (int j = 0; j < TA; ++j) {
+        const int k1 = j * A + kq;
+#pragma unroll
+        for (int ap = 0; ap < A; ++ap) uu[j][ap] = ld2(&X[k1 * P1 + b + B * ap]);
+        dftn<A>(uu[j], +1);
+#pragma unroll
+        for (int c = 1; c < A; ++c) uu[j][c] = cmul(uu[j][c], ldg2(&tw2[c * B2 + b]));
+    }
+    sync();
+#pragma unroll
+    for (int j = 0; j < TA; ++j) {
+        const int k1 = j * A + kq;
+#pragma unroll
+        for (int c = 0; c < A; ++c) st2(&X[k1 * Q + c * Bp + b], uu[j][c]);
+    }
+    }
+    sync();
+    // pass 2b: task (k1 = j B + kq2, c); the B threads store their values
+    // back where they read them
+    const int c = C::SW ? t / B : t % A, kq2 = C::SW ? t % B : t / A;
+    cx<float> v[TB][B];
+#pragma unroll
+    for (int j = 0; j < TB; ++j) {
+        const int k1 = j * B + kq2;
+#pragma unroll
+        for (int bb = 0; bb < B; ++bb) v[j][bb] = ld2(&X[k1 * Q + c * Bp + bb]);
+        dftn<B>(v[j], +1);
+        if (h == 1) {
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb) st2(&X[k1 * Q + c * Bp + bb], v[j][bb]);
+        }
+    }
+    sync();
+    if (h == 0) {
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+            const int k1 = j * B + kq2;
+#pragma unroll
+            for (int d = 0; d < B; ++d) {
+                // zeta = Re A, u_theta = Im A, u_phi = Re B;  W = (-q u_phi, q u_theta)
+                const cx<float> zb = ld2(&XB[k1 * Q + c * Bp + d]);
+                const float q = v[j][d].x + fc;
+                v[j][d] = {-q * zb.x, q * v[j][d].y};
+            }
+            dftn<B>(v[j], -1);
+#pragma unroll
+            for (int bb = 1; bb < B; ++bb) v[j][bb] = cmul(v[j][bb], conjg2(&tw2[c * B2 + bb]));
+#pragma unroll
+            for (int bb = 0; bb < B; ++bb) st2(&XA[k1 * Q + c * Bp + bb], v[j][bb]);
+        }
+    }
+    sync();
+    // the B buffers are free from here: the remaining passes alternate
+    // between XA and XB, so each needs one barrier
+    if (h == 0) {
+        // A-point DFT over c -> a', twiddle e^{-2 pi i t k1 / M} with t = b + B a'
+#pragma unroll
+        for (int j = 0; j < TA; ++j) {
+            const int k1 = j * A + kq;
+            cx<float> y[A];
+#pragma unroll
+            for (int cc = 0; cc < A; ++cc) y[cc] = ld2(&XA[k1 * Q + cc * Bp + b]);
+            dftn<A>(y, -1);
+#pragma unroll
+            for (int ap = 0; ap < A; ++ap) st2(&XB[k1 * P1 + b + B * ap], cmul(y[ap], conjg2(&tw1[k1 * P1 + b + B * ap])));
+        }
+    }
+    sync();
+    // 24-point DFT over k1 -> W's spectrum at n = t + M2 n1 (only m <= N and
+    // m >= M - N are read back: n1 = 8 .. 15 are never needed)
+    if (h == 0) {
+        cx<float> y[24];
+#pragma unroll
+        for (int k1 = 0; k1 < 24; ++k1) y[k1] = ld2(&XB[k1 * P1 + t]);
+        dft24<-1>(y);
+#pragma unroll
+        for (int n1 = 0; n1 < 24; ++n1)
+            if (n1 < 8 || n1 >= 16) st2(&XA[t + M2 * n1], y[n1]);
+    }
+    sync();
+
+    // separate the two real fields, truncate to m <= N, weight, store
+    for (int i = tid; i < ld * GP; i += NT) {
         const int rp = i % GP, m = i / GP;
         const int l = lat0 + 2 * rp;
         if (l >= nlat) continue;
