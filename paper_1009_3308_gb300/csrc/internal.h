@@ -213,6 +213,7 @@ struct sphnse_plan {
     // device constants
     double* d_x = nullptr;       // cos(theta_p), nlat
     double* d_s = nullptr;       // sin(theta_p), nlat
+    float* d_isin32 = nullptr;   // 1 / sin(theta_p) rounded to FP32, nlat
     double* d_rw = nullptr;      // (2 pi / M) w_p / sin(theta_p), nlat
     double* d_tw = nullptr;      // e^{-2 pi i t / M}, M complex (FP64)
     float* d_tw32 = nullptr;     // same in FP32

@@ -540,7 +540,7 @@ struct TcSynArgs {
     const unsigned char* btiles; // [group][tile][brows][64] bf16, 128-byte swizzle (k_prep_tc)
     const int* tile_off;         // first tile of block b = 2 m + parity
     float* gsyn;                 // instance i writes gsyn + i * sgs complex entries
-    const double* sinth;
+    const float* isin;           // 1 / sin(theta_p), FP32
     unsigned* status;
     int N, nh, nlat, nblk, pairs;
     int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
@@ -598,13 +598,17 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + ns * bbytes);
     uint64_t* a_full = bars;
     uint64_t* a_empty = bars + ns;
+    // accumulator buffers: the single-instance kernel has four (16 columns
+    // per parity each), so that an item's epilogue, which waits on global
+    // loads and stores, never holds up the MMAs of the items after it
+    constexpr int NACC = SINGLE ? 4 : 2;
     uint64_t* acc_full = bars + 2 * ns;
-    uint64_t* acc_empty = acc_full + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 4);
+    uint64_t* acc_empty = acc_full + NACC;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NACC);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     uint32_t tcols = 32;
-    while (tcols < uint32_t(4 * brows)) tcols <<= 1;
+    while (tcols < uint32_t(2 * NACC * brows)) tcols <<= 1;
     constexpr uint16_t cmask = uint16_t((1u << CS) - 1u);
     const int crank = CS > 1 ? int(cluster_ctarank()) : 0;
     if (threadIdx.x == 0) {
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             mbar_init(&a_full[s], 1);
             mbar_init(&a_empty[s], CS);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
         }
@@ -703,9 +707,9 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int m = a.items[ib + i].x, mt = a.items[ib + i].y;
-                const int buf = i & 1, use = i >> 1;
+                const int buf = i % NACC, use = i / NACC;
                 bool ok = true;
-                if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
+                if (i >= NACC) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
                     const int nkt = syn_nkt(N, m, par), nd = syn_ndeg(N, m, par);
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
                 }
                 mma_commit(&acc_full[buf]);
             }
-            if (nI > 0) mbar_wait(&acc_full[(nI - 1) & 1], ((nI - 1) >> 1) & 1, abort, a.status);
+            if (nI > 0) mbar_wait(&acc_full[(nI - 1) % NACC], ((nI - 1) / NACC) & 1, abort, a.status);
         }
     } else {
         pdl_wait();
@@ -739,18 +743,20 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         (void)ld;
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
-            const int m = itm.x, mt = itm.y, g = itm.z * CS + crank, buf = i & 1;
+            const int m = itm.x, mt = itm.y, g = itm.z * CS + crank, buf = i % NACC;
             const int ngi = SINGLE ? 1 : max(0, min(a.ng, a.nb - g * a.ng));
-            const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
-            tc_fence_after();
+            // the item's constants are loaded before the wait, so their
+            // latency passes while the MMAs run
             const float mm = float(m);
             const int p = mt * TC_TILE_M + quarter * 32 + lane;
             const uint32_t lanes = uint32_t(quarter * 32) << 16;
-            const float inv_s = p < nh ? float(1.0 / a.sinth[p]) : 0.f;
+            const float inv_s = p < nh ? a.isin[p] : 0.f;
             // a parity whose table tiles are all negligible at this latitude
             // tile had no MMA: its accumulator holds no data and counts as 0
             const bool zE = a.kt0[(2 * m) * a.nmt + mt] >= syn_nkt(N, m, 0);
             const bool zO = a.kt0[(2 * m + 1) * a.nmt + mt] >= syn_nkt(N, m, 1);
+            const bool ok = mbar_wait(&acc_full[buf], (i / NACC) & 1, abort, a.status);
+            tc_fence_after();
             for (int q = 0; q < ngi; ++q) {
                 uint32_t e[12], o[12];
                 const uint32_t ce = tmem + lanes + uint32_t((buf * 2 + 0) * brows + 12 * q);
@@ -1349,7 +1355,7 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     const auto& T = P->tc;
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(T.smap_hi), reinterpret_cast<const CUtensorMap*>(T.smap_lo),
                 B.items, B.off, B.btiles, T.tile_off, gsyn,
-                P->d_s, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
+                P->d_isin32, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
                 B.ng, B.nb, B.brows, T.ntiles, B.ns, sg_floats / 2, T.syn_kt0, T.syn_nmt,
                 reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_hi_c2 : T.smap_hi_c4),
                 reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_lo_c2 : T.smap_lo_c4)};

@@ -204,7 +204,7 @@ static void destroy_plan(sphnse_plan* P) {
     if (P->d_info) cudaFree(P->d_info);
     if (P->h_info) cudaFreeHost(P->h_info);
     void* ptrs[] = {P->d_items, P->d_item_off, P->d_status,
-                    P->d_x, P->d_s, P->d_rw, P->d_tw, P->d_tw32, P->d_ftw, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
+                    P->d_x, P->d_s, P->d_isin32, P->d_rw, P->d_tw, P->d_tw32, P->d_ftw, P->d_lm, P->d_finc, P->d_prepc, P->d_finc32, P->d_prepc32, P->d_bsyn,
                     P->d_gsyn, P->d_gana, P->d_hana, P->d_gsyn_r, P->d_gana_r, P->d_grid, P->d_theta, P->d_w, P->d_work, P->d_tmp, P->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -322,6 +322,7 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     const size_t sz_g = size_t(nlat) * (L + 1) * 2 * sizeof(double);
     if (!rc) rc = dalloc(&P->d_x, nlat * sizeof(double));
     if (!rc) rc = dalloc(&P->d_s, nlat * sizeof(double));
+    if (!rc) rc = dalloc(&P->d_isin32, nlat * sizeof(float));
     if (!rc) rc = dalloc(&P->d_rw, nlat * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tw, tw.size() * sizeof(double));
     if (!rc) rc = dalloc(&P->d_tw32, tw32.size() * sizeof(float));
@@ -348,6 +349,11 @@ sphnse_plan* sphnse_plan_create(int L, int nlat, int nlon, double nu, double Ome
     };
     up(P->d_x, P->x.data(), nlat * sizeof(double));
     up(P->d_s, P->s.data(), nlat * sizeof(double));
+    {
+        std::vector<float> isin(nlat);
+        for (int p = 0; p < nlat; ++p) isin[p] = float(1.0 / P->s[p]);
+        up(P->d_isin32, isin.data(), nlat * sizeof(float));
+    }
     up(P->d_rw, rw.data(), nlat * sizeof(double));
     up(P->d_tw, tw.data(), tw.size() * sizeof(double));
     up(P->d_tw32, tw32.data(), tw32.size() * sizeof(float));
