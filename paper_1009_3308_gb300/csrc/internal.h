@@ -306,8 +306,9 @@ bool stream_ok(const sphnse_plan* P, int prec);
 int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec, int pairs = 0);
 bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
-int launch_synthesis_tc(sphnse_plan* P, int pairs);
-int launch_prep_tc(sphnse_plan* P, const double* alpha);
+// coefficient prep and synthesis of the plan's own instance (alpha: packed
+// coefficients on the device)
+int launch_synthesis_tc(sphnse_plan* P, const double* alpha, int pairs);
 // batched tcgen05 synthesis over nb instances of P's truncation (ensembles)
 int tc_setup_synthesis(sphnse_plan* P);
 // instance groups of at most ngmax (<= 9) instances, at most nsmax (<= 6)
@@ -315,7 +316,8 @@ int tc_setup_synthesis(sphnse_plan* P);
 int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax = 9, int nsmax = 6, int cs = 1);
 void tc_batch_free(TcBatch* B);
 int launch_prep_tc_batch(sphnse_plan* P, const TcBatch& B, const double* alpha);
-int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs);
+int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs,
+                              const double* alpha = nullptr);
 int tc_setup_analysis(sphnse_plan* P, int nf);
 int tc_batch_ana_init(sphnse_plan* P, int nb, TcBatchA* B);
 void tc_batch_ana_free(TcBatchA* B);

@@ -298,9 +298,14 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
                            const int2* __restrict__ lm, const float4* __restrict__ finc, int N, double nu, int n,
                            size_t hstride, const double* __restrict__ nu_inst, double omega_d) {
     pdl_launch();
-    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // the plan's constants are read before the wait for the predecessor
+    int L, m;
+    packed_lm(N, i, L, m);
+    (void)lm;
+    const float4 c = finc[i];
+    pdl_wait();
     // batch of instances along gridDim.y: per-instance vectors, projections, nu
     {
         const size_t b = blockIdx.y;
@@ -310,10 +315,6 @@ __global__ void k_finish32(int kind, const float* __restrict__ hana, int nf, con
         if (forcing) forcing += b * n;
         if (nu_inst) nu = nu_inst[b];
     }
-    int L, m;
-    packed_lm(N, i, L, m);
-    (void)lm;
-    const float4 c = finc[i];
     const float* hL = hana + size_t(ext_row(N, m, L)) * 2 * nf;
     const float* hU = hana + size_t(ext_row(N, m, L + 1)) * 2 * nf;
     const float* hD = L - 1 >= m ? hana + size_t(ext_row(N, m, L - 1)) * 2 * nf : nullptr;

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "f64cvt.h"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -523,6 +524,136 @@ __global__ void __launch_bounds__(192, 1) k_ana_tc_b(TcAnaBArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// coefficient sets of the synthesis
+//
+// zeta: lam^{1/2} a_K; theta: lam^{-1/2} a_K; phi: c_down a_{K-1} + c_up
+// a_{K+1}, the degree-shift form of sin(theta) d/dtheta, for chunk q of K
+// tile kt of block (m, parity): the 8 degrees K = m + par + 2 j, j = 64 kt +
+// 8 q .. +7.  prep_consts reads the plan's table (before any wait for the
+// predecessor); prep_chunk reads alpha and returns the hi parts of the six
+// columns (v[0..5]), their lo parts (v[6..11]) and, for m = 1, the u_phi at
+// m = 0 column -a_{K,0} (hi v[12], lo v[13]; zero otherwise).  With
+// d/dtheta Pt_K^0 = sqrt(K (K+1)) Pt_K^1 (ladder relation, Condon-Shortley
+// phase), u_phi at m = 0 is -sum_K alpha_{K,0} Pt_K^1: a sum over the
+// order-1 table that needs no division by sin(theta).
+__device__ __forceinline__ void prep_consts(const float4* __restrict__ prepc, int N, int m, int par, int kt, int q,
+                                            float4 (&cf)[8]) {
+    const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
+    const int j0 = kt * TC_TILE_K + q * 8;
+    const int r0 = ext_off(N, m) + (par ? ne : 0);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) cf[e] = (j0 + e < n) ? prepc[r0 + j0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void prep_chunk(const double2* __restrict__ alpha, int N, int m, int par, int kt, int q,
+                                           const float4 (&cf)[8], uint4 (&v)[14]) {
+    const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
+    const int j0 = kt * TC_TILE_K + q * 8;
+    const int lo = m > 0 ? m : 1;
+    const int K0 = m + par + 2 * j0;
+    const int pk = packed_off(N, m) - lo;   // packed index of degree K is pk + K
+    float2 al[17];
+#pragma unroll
+    for (int e = 0; e < 17; ++e) {
+        const int K = K0 - 1 + e;
+        double2 x = make_double2(0.0, 0.0);
+        if (K >= lo && K <= N) x = alpha[pk + K];
+        al[e] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+    }
+    float c6[6][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float2 am = al[2 * e], a0 = al[2 * e + 1], ap = al[2 * e + 2];
+        c6[0][e] = cf[e].x * a0.x;
+        c6[1][e] = cf[e].x * a0.y;
+        c6[2][e] = cf[e].y * a0.x;
+        c6[3][e] = cf[e].y * a0.y;
+        c6[4][e] = fmaf(cf[e].z, am.x, cf[e].w * ap.x);
+        c6[5][e] = fmaf(cf[e].z, am.y, cf[e].w * ap.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        v[c] = pack_hi(c6[c]);
+        v[6 + c] = pack_lo(c6[c]);
+    }
+    v[12] = v[13] = make_uint4(0u, 0u, 0u, 0u);
+    if (m == 1) {
+        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N (real)
+        float re[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int K = K0 + 2 * e;
+            re[e] = (j0 + e < n && K <= N) ? -f64_to_f32_rn(a0[K].x) : 0.f;
+        }
+        v[12] = pack_hi(re);
+        v[13] = pack_lo(re);
+    }
+}
+
+// The same coefficient sets split over the four lanes (q, p) of a chunk:
+// lane p takes the degrees j = 64 kt + 8 q + 2 p, +1 and returns word p (two
+// bf16) of each row of the chunk: hi parts w[0..5], lo parts w[6..11], the
+// u_phi at m = 0 column (m = 1 only) w[12] (hi), w[13] (lo).
+__device__ __forceinline__ void prep_words(const double2* __restrict__ alpha, const float4* __restrict__ prepc, int N,
+                                           int m, int par, int kt, int q, int p, uint32_t (&w)[14]) {
+    const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
+    const int j0 = kt * TC_TILE_K + q * 8 + 2 * p;
+    const int r0 = ext_off(N, m) + (par ? ne : 0);
+    const int lo = m > 0 ? m : 1;
+    const int K0 = m + par + 2 * j0;          // degree of j0
+    const int pk = packed_off(N, m) - lo;     // packed index of degree K is pk + K
+    float4 cf[2];
+    float2 al[5];                             // degrees K0 - 1 .. K0 + 3
+#pragma unroll
+    for (int e = 0; e < 2; ++e) cf[e] = (j0 + e < n) ? prepc[r0 + j0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+        const int K = K0 - 1 + e;
+        double2 x = make_double2(0.0, 0.0);
+        if (K >= lo && K <= N) x = alpha[pk + K];
+        al[e] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+    }
+    float c6[6][2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float2 am = al[2 * e], a0 = al[2 * e + 1], ap = al[2 * e + 2];
+        c6[0][e] = cf[e].x * a0.x;
+        c6[1][e] = cf[e].x * a0.y;
+        c6[2][e] = cf[e].y * a0.x;
+        c6[3][e] = cf[e].y * a0.y;
+        c6[4][e] = fmaf(cf[e].z, am.x, cf[e].w * ap.x);
+        c6[5][e] = fmaf(cf[e].z, am.y, cf[e].w * ap.y);
+    }
+    auto hi2 = [](float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    };
+    auto lo2 = [](float a, float b) {
+        const float la = a - __bfloat162float(__float2bfloat16_rn(a));
+        const float lb = b - __bfloat162float(__float2bfloat16_rn(b));
+        const __nv_bfloat162 l = __floats2bfloat162_rn(la, lb);
+        return *reinterpret_cast<const uint32_t*>(&l);
+    };
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        w[c] = hi2(c6[c][0], c6[c][1]);
+        w[6 + c] = lo2(c6[c][0], c6[c][1]);
+    }
+    w[12] = w[13] = 0u;
+    if (m == 1) {
+        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N (real)
+        float re[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int K = K0 + 2 * e;
+            re[e] = (j0 + e < n && K <= N) ? -f64_to_f32_rn(a0[K].x) : 0.f;
+        }
+        w[12] = hi2(re[0], re[1]);
+        w[13] = lo2(re[0], re[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // synthesis
 //
 // Per order m and parity: g[p][c] = sum_j Pt_{K_j}^m(x_p) b[j][c], the dense
@@ -550,9 +681,14 @@ struct TcSynArgs {
     // clusters of CS > 1 CTAs: maps of the same blocks with boxes of 128 / CS latitudes
     const CUtensorMap* map_hi_cs;
     const CUtensorMap* map_lo_cs;
+    // SINGLE: the coefficients the builder warps read
+    const double2* alpha;
+    const float4* prepc;
 };
 
 constexpr int TC_SYN_MAXNS = 8;
+constexpr int TC_SYN_SMITEMS = 64;   // items per CTA kept in shared memory
+constexpr int TC_SYN_BUILDERS = 6;   // warps building coefficient tiles (single-instance synthesis)
 
 __host__ __device__ inline int syn_ndeg(int N, int m, int par) {
     const int n = par ? ext_odd(N, m) : ext_even(N, m);
@@ -585,7 +721,7 @@ __host__ __device__ inline int syn_tailw(int N, int m, int par) {
 // of the cluster are done with it (their commits arrive on each CTA's empty
 // barrier).
 template <int NS, bool SINGLE, int CS = 1>
-__global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
+__global__ void __launch_bounds__(SINGLE ? 192 + 32 * TC_SYN_BUILDERS : 192, 1) k_syn_tc(TcSynArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
@@ -604,8 +740,13 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     constexpr int NACC = SINGLE ? 4 : 2;
     uint64_t* acc_full = bars + 2 * ns;
     uint64_t* acc_empty = acc_full + NACC;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NACC);
+    uint64_t* b_full = acc_empty + NACC;                         // SINGLE: coefficient tile of a stage built
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + (SINGLE ? ns : 0));
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // the CTA's first TC_SYN_SMITEMS items, (m, latitude tile, group, first
+    // K tile of the even | odd block << 16), read once: every role walks the
+    // item list, and dependent global loads per item would stall it
+    int4* s_items = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(bars) + 512);
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     uint32_t tcols = 32;
     while (tcols < uint32_t(2 * NACC * brows)) tcols <<= 1;
@@ -615,6 +756,7 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         for (int s = 0; s < ns; ++s) {
             mbar_init(&a_full[s], 1);
             mbar_init(&a_empty[s], CS);
+            if constexpr (SINGLE) mbar_init(&b_full[s], 1);
         }
         for (int b = 0; b < NACC; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -623,6 +765,18 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
         *abort = 0;
         fence_barrier_init();
     }
+    const int ib = a.item_off[blockIdx.x / CS], nI = a.item_off[blockIdx.x / CS + 1] - ib;
+    for (int j = threadIdx.x; j < nI && j < TC_SYN_SMITEMS; j += blockDim.x) {
+        const int4 itm = a.items[ib + j];
+        const int e = a.kt0[(2 * itm.x) * a.nmt + itm.y], o = a.kt0[(2 * itm.x + 1) * a.nmt + itm.y];
+        s_items[j] = make_int4(itm.x, itm.y, itm.z, e | (o << 16));
+    }
+    auto item_meta = [&](int i) -> int4 {
+        if (i < TC_SYN_SMITEMS) return s_items[i];
+        const int4 itm = a.items[ib + i];
+        const int e = a.kt0[(2 * itm.x) * a.nmt + itm.y], o = a.kt0[(2 * itm.x + 1) * a.nmt + itm.y];
+        return make_int4(itm.x, itm.y, itm.z, e | (o << 16));
+    };
     if (warp == 1) {
         tmem_alloc(tmem_slot, tcols);
         tmem_relinquish();
@@ -633,11 +787,38 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int ib = a.item_off[blockIdx.x / CS], nI = a.item_off[blockIdx.x / CS + 1] - ib;
     const int N = a.N, nh = a.nh, nlat = a.nlat;
     pdl_launch();
 
-    if (warp == 0) {
+    if (warp == 0 && SINGLE) {
+        if (lane == 0) {
+            // the table does not depend on the predecessor (no wait); the
+            // builder warps write every stage's coefficient tile
+            const uint64_t pol = policy_evict_first();
+            int it = 0;
+            for (int i = 0; i < nI; ++i) {
+                const int4 itm = item_meta(i);
+                const int m = itm.x, mt = itm.y;
+                for (int par = 0; par < 2; ++par) {
+                    const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
+                    const int tw = syn_tailw(N, m, par);
+                    for (int kt = ((itm.w >> (16 * par)) & 0xFFFF); kt < nkt; ++kt, ++it) {
+                        const int s = it % ns;
+                        if (it >= ns && !mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
+                        if (*abort) continue;
+                        const bool last = kt == nkt - 1;
+                        const int w = last ? tw : TC_TILE_K;
+                        const int mi = last ? a.nblk + b : b;
+                        mbar_arrive_expect_tx(&a_full[s], uint32_t(2 * w * TC_TILE_M * 2));
+                        tma_load_2d(A_hi + s * TC_ATILE, &a.map_hi[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                        tma_load_2d(A_lo + s * TC_ATILE, &a.map_lo[mi], kt * TC_TILE_K, mt * TC_TILE_M, &a_full[s], pol);
+                    }
+                }
+            }
+            for (int k = it - ns; k < it; ++k)
+                if (k >= 0) mbar_wait(&a_full[k % ns], (k / ns) & 1, abort, a.status);
+        }
+    } else if (warp == 0) {
         if (lane == 0) {
             // the table tiles of the first ns stages do not depend on the
             // predecessor (the B tiles do): they are requested before the wait,
@@ -650,14 +831,14 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             bool waited = false;
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int4 itm = a.items[ib + i];
+                const int4 itm = item_meta(i);
                 const int m = itm.x, mt = itm.y, g = itm.z * CS + crank;
                 for (int par = 0; par < 2; ++par) {
                     const int b = 2 * m + par, nkt = syn_nkt(N, m, par);
                     const int tw = syn_tailw(N, m, par);
                     const unsigned char* bsrc =
                         a.btiles + (size_t(g) * a.ntiles + size_t(a.tile_off[b])) * size_t(bbytes);
-                    for (int kt = a.kt0[b * a.nmt + mt]; kt < nkt; ++kt, ++it) {
+                    for (int kt = ((itm.w >> (16 * par)) & 0xFFFF); kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
                         if (it >= ns) {
                             if (!waited) {
@@ -706,18 +887,20 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const uint32_t idesc = idesc_bf16(TC_TILE_M, brows);
             int it = 0;
             for (int i = 0; i < nI; ++i) {
-                const int m = a.items[ib + i].x, mt = a.items[ib + i].y;
+                const int4 itm = item_meta(i);
+                const int m = itm.x, mt = itm.y;
                 const int buf = i % NACC, use = i / NACC;
                 bool ok = true;
                 if (i >= NACC) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status);
                 tc_fence_after();
                 for (int par = 0; par < 2; ++par) {
                     const int nkt = syn_nkt(N, m, par), nd = syn_ndeg(N, m, par);
-                    const int kt0 = a.kt0[(2 * m + par) * a.nmt + mt];
+                    const int kt0 = (itm.w >> (16 * par)) & 0xFFFF;
                     const uint32_t d = tmem + uint32_t((buf * 2 + par) * brows);
                     for (int kt = kt0; kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
-                        const bool okA = mbar_wait(&a_full[s], (it / ns) & 1, abort, a.status);
+                        bool okA = mbar_wait(&a_full[s], (it / ns) & 1, abort, a.status);
+                        if constexpr (SINGLE) okA = okA && mbar_wait(&b_full[s], (it / ns) & 1, abort, a.status);
                         tc_fence_after();
                         // 16-degree chunks of this K tile that hold degrees of the block
                         const int nkk = min(TC_TILE_K, nd - kt * TC_TILE_K + 15) / 16;
@@ -736,13 +919,13 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             }
             if (nI > 0) mbar_wait(&acc_full[(nI - 1) % NACC], ((nI - 1) / NACC) & 1, abort, a.status);
         }
-    } else {
+    } else if (warp < 6) {
         pdl_wait();
         const int quarter = warp & 3;
         const size_t ld = size_t(N + 1);
         (void)ld;
         for (int i = 0; i < nI; ++i) {
-            const int4 itm = a.items[ib + i];
+            const int4 itm = item_meta(i);
             const int m = itm.x, mt = itm.y, g = itm.z * CS + crank, buf = i % NACC;
             const int ngi = SINGLE ? 1 : max(0, min(a.ng, a.nb - g * a.ng));
             // the item's constants are loaded before the wait, so their
@@ -753,8 +936,8 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             const float inv_s = p < nh ? a.isin[p] : 0.f;
             // a parity whose table tiles are all negligible at this latitude
             // tile had no MMA: its accumulator holds no data and counts as 0
-            const bool zE = a.kt0[(2 * m) * a.nmt + mt] >= syn_nkt(N, m, 0);
-            const bool zO = a.kt0[(2 * m + 1) * a.nmt + mt] >= syn_nkt(N, m, 1);
+            const bool zE = (itm.w & 0xFFFF) >= syn_nkt(N, m, 0);
+            const bool zO = (itm.w >> 16) >= syn_nkt(N, m, 1);
             const bool ok = mbar_wait(&acc_full[buf], (i / NACC) & 1, abort, a.status);
             tc_fence_after();
             for (int q = 0; q < ngi; ++q) {
@@ -809,6 +992,47 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
         }
+    } else if constexpr (SINGLE) {
+        // builders (warps 6 .. 5 + TC_SYN_BUILDERS): warp 6 + it % TC_SYN_BUILDERS writes stage it's
+        // coefficient tile once the stage's slot is free, lane (q, p) word p
+        // of chunk q of every row, and announces it on b_full
+        // A builder starts on stage it only after its previous stage, it -
+        // TC_SYN_BUILDERS, was stored, i.e. after stage it - TC_SYN_BUILDERS
+        // - ns was consumed.  Its parity wait for the release of stage it -
+        // ns is only unambiguous if stage it - 2 ns was consumed as well,
+        // which needs TC_SYN_BUILDERS <= ns.
+        static_assert(TC_SYN_BUILDERS <= NS, "builders may not run a full ring ahead");
+        const int bw = warp - 6, q = lane >> 2, p = lane & 3;
+        bool waited = false;
+        int it = 0;
+        for (int i = 0; i < nI; ++i) {
+            const int4 itm = item_meta(i);
+            const int m = itm.x;
+            for (int par = 0; par < 2; ++par) {
+                const int nkt = syn_nkt(N, m, par);
+                for (int kt = ((itm.w >> (16 * par)) & 0xFFFF); kt < nkt; ++kt, ++it) {
+                    if (it % TC_SYN_BUILDERS != bw) continue;
+                    const int s = it % ns;
+                    if (!waited) {
+                        pdl_wait();   // alpha may be the predecessor's output
+                        waited = true;
+                    }
+                    // the values first: their loads pass while the slot drains
+                    uint32_t w[14];
+                    prep_words(a.alpha, a.prepc, N, m, par, kt, q, p, w);
+                    if (it >= ns && !mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
+                    if (*abort) continue;
+                    unsigned char* tile = Bs + s * bbytes;
+#pragma unroll
+                    for (int r = 0; r < 14; ++r) *reinterpret_cast<uint32_t*>(tile + sw128_chunk(r, q) + 4 * p) = w[r];
+                    *reinterpret_cast<uint32_t*>(tile + sw128_chunk(14, q) + 4 * p) = 0u;
+                    *reinterpret_cast<uint32_t*>(tile + sw128_chunk(15, q) + 4 * p) = 0u;
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&b_full[s]);
+                }
+            }
+        }
     }
     tc_fence_before();
     // no CTA leaves while another of its cluster may still write its shared memory
@@ -820,79 +1044,36 @@ __global__ void __launch_bounds__(192, 1) k_syn_tc(TcSynArgs a) {
     }
 }
 
-// Coefficient sets of the synthesis (zeta: lam^{1/2} a_K; theta: lam^{-1/2}
-// a_K; phi: c_down a_{K-1} + c_up a_{K+1}, the degree-shift form of
-// sin(theta) d/dtheta), written as the B tiles of k_syn_tc.  Thread (tile,
-// chunk q) of instance blockIdx.y computes the 8 degrees K = m + par + 2 j,
-// j = 64 kt + 8 q .. +7, of block b = (m, parity), and stores the hi parts of
-// the six columns in rows r0 .. r0+5 and the lo parts in rows r0+6 .. r0+11,
-// r0 = 12 (instance mod ng), of its group's tile (rows past the group's
-// instances stay zero).  All of a thread's loads are independent.
-//
-// Every instance also has two rows 12 ng + 2 (instance mod ng) (hi, lo) that
-// only the order-1 tiles fill, with the real column -a_{K,0}.  With
-// d/dtheta Pt_K^0 = sqrt(K (K+1)) Pt_K^1 (ladder relation, Condon-Shortley
-// phase), u_phi at m = 0 is -sum_K alpha_{K,0} Pt_K^1: a sum over the
-// order-1 table that needs no division by sin(theta).  The degree-shift form
-// of the m = 0 column cancels to O(sin^2 theta) near the poles, where the
-// split's rounding would be amplified by 1 / sin(theta).
+// B tiles of the batched synthesis: thread (tile, chunk q) of instance
+// blockIdx.y stores the chunk's hi parts in rows r0 .. r0+5 and lo parts in
+// rows r0+6 .. r0+11, r0 = 12 (instance mod ng), of its group's tile, and on
+// order-1 tiles the u_phi at m = 0 column in rows 12 ng + 2 (instance mod
+// ng) (hi, lo); rows past the group's instances stay zero.
 __global__ void __launch_bounds__(128) k_prep_tc(const double2* __restrict__ alpha, const float4* __restrict__ prepc,
                                                  unsigned char* __restrict__ btiles, const int2* __restrict__ tinfo,
                                                  int ntiles, int N, int n_coeff, int ng, int brows) {
     pdl_launch();
-    pdl_wait();   // alpha may be the predecessor's output
     const int g = blockIdx.x * 16 + (threadIdx.x >> 3), q = threadIdx.x & 7;
     if (g >= ntiles) return;
     const int inst = blockIdx.y;
     alpha += size_t(inst) * n_coeff;
     const int2 ti = tinfo[g];
     const int b = ti.x, kt = ti.y, m = b >> 1, par = b & 1;
-    const int ne = ext_even(N, m), n = par ? ext_odd(N, m) : ne;
-    const int j0 = kt * TC_TILE_K + q * 8;
-    const int lo = m > 0 ? m : 1;
-    const int K0 = m + par + 2 * j0;
-    const int pk = packed_off(N, m) - lo;   // packed index of degree K is pk + K
-    const int r0 = ext_off(N, m) + (par ? ne : 0);
-    float2 al[17];
-#pragma unroll
-    for (int e = 0; e < 17; ++e) {
-        const int K = K0 - 1 + e;
-        double2 v = make_double2(0.0, 0.0);
-        if (K >= lo && K <= N) v = alpha[pk + K];
-        al[e] = make_float2(float(v.x), float(v.y));
-    }
+    // the plan's table is read before the wait; alpha may be the
+    // predecessor's output
     float4 cf[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) cf[e] = (j0 + e < n) ? prepc[r0 + j0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float v[6][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float2 am = al[2 * e], a0 = al[2 * e + 1], ap = al[2 * e + 2];
-        v[0][e] = cf[e].x * a0.x;
-        v[1][e] = cf[e].x * a0.y;
-        v[2][e] = cf[e].y * a0.x;
-        v[3][e] = cf[e].y * a0.y;
-        v[4][e] = fmaf(cf[e].z, am.x, cf[e].w * ap.x);
-        v[5][e] = fmaf(cf[e].z, am.y, cf[e].w * ap.y);
-    }
+    prep_consts(prepc, N, m, par, kt, q, cf);
+    pdl_wait();
+    uint4 v[14];
+    prep_chunk(alpha, N, m, par, kt, q, cf, v);
     const int grp = inst / ng, row0 = 12 * (inst % ng);
     unsigned char* tile = btiles + (size_t(grp) * ntiles + g) * size_t(brows) * TC_TILE_K * 2;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + c, q)) = pack_hi(v[c]);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + 6 + c, q)) = pack_lo(v[c]);
-    }
+    for (int c = 0; c < 12; ++c) *reinterpret_cast<uint4*>(tile + sw128_chunk(row0 + c, q)) = v[c];
     if (m == 1) {
-        const double2* a0 = alpha + (packed_off(N, 0) - 1);   // a_{K,0} at a0[K], K = 1 .. N (real)
-        float re[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int K = K0 + 2 * e;
-            re[e] = (j0 + e < n && K <= N) ? -float(a0[K].x) : 0.f;
-        }
         const int rp = 12 * ng + 2 * (inst % ng);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp, q)) = pack_hi(re);
-        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp + 1, q)) = pack_lo(re);
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp, q)) = v[12];
+        *reinterpret_cast<uint4*>(tile + sw128_chunk(rp + 1, q)) = v[13];
     }
 }
 
@@ -1226,7 +1407,7 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax, int 
     T.ng = (nb + T.ngroups - 1) / T.ngroups;   // balanced groups
     T.brows = ((14 * T.ng + 15) / 16) * 16;
     const size_t stage = 2 * size_t(TC_ATILE) + size_t(T.brows) * TC_TILE_K * 2;
-    T.ns = int(std::min<size_t>(std::min(nsmax, 6), (size_t(227) * 1024 - 1024 - 512) / stage));
+    T.ns = int(std::min<size_t>(std::min(nsmax, 6), (size_t(227) * 1024 - 1024 - 512 - TC_SYN_SMITEMS * sizeof(int4)) / stage));
     if (cs > 1) {
         // slice maps (128 / cs latitudes per box) of this plan, once
         void** hi = cs == 2 ? &P->tc.smap_hi_c2 : &P->tc.smap_hi_c4;
@@ -1345,10 +1526,14 @@ static int syn_cluster_capacity(int ns, int cs, size_t smem) {
     return n;
 }
 
-int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs) {
-    const size_t sm = 1024 + size_t(B.ns) * (2 * size_t(TC_ATILE) + size_t(B.brows) * TC_TILE_K * 2) + 512;
+int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, size_t sg_floats, int pairs,
+                              const double* alpha) {
+    // 1 KB alignment slack, the stages, 512 B of barriers, the item table
+    const size_t sm = 1024 + size_t(B.ns) * (2 * size_t(TC_ATILE) + size_t(B.brows) * TC_TILE_K * 2) + 512 +
+                      TC_SYN_SMITEMS * sizeof(int4);
     if (sm > 227 * 1024 || B.ns > TC_SYN_MAXNS) return SPHNSE_E_UNSUPPORTED;
-    const bool single = B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1;
+    // one instance with alpha given: the kernel builds its coefficient tiles
+    const bool single = alpha && B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1;
     SynKernel kern = syn_kernel(B.ns, single, B.cs);
     if (!kern) return SPHNSE_E_UNSUPPORTED;
     allow_dynamic_smem(reinterpret_cast<const void*>(kern), sm);
@@ -1358,16 +1543,18 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
                 P->d_isin32, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
                 B.ng, B.nb, B.brows, T.ntiles, B.ns, sg_floats / 2, T.syn_kt0, T.syn_nmt,
                 reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_hi_c2 : T.smap_hi_c4),
-                reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_lo_c2 : T.smap_lo_c4)};
+                reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_lo_c2 : T.smap_lo_c4),
+                reinterpret_cast<const double2*>(alpha), P->d_prepc32};
+    const int threads = single ? 192 + 32 * TC_SYN_BUILDERS : 192;
     stage_begin(P, SPHNSE_STAGE_SYNTHESIS);
     cudaError_t e;
     if (B.cs == 1) {
-        e = launch_pdl(kern, dim3(B.ncta), dim3(192), sm, P->stream, a);
+        e = launch_pdl(kern, dim3(B.ncta), dim3(threads), sm, P->stream, a);
     } else {
         prefer_max_smem(reinterpret_cast<const void*>(kern));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(B.ncta);
-        cfg.blockDim = dim3(192);
+        cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = sm;
         cfg.stream = P->stream;
         cudaLaunchAttribute attr[2];
@@ -1385,16 +1572,18 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     return check_cuda(e);
 }
 
-int launch_prep_tc(sphnse_plan* P, const double* alpha) {
+// The plan's own instance: the synthesis builds its coefficient tiles from
+// alpha itself (no prep kernel, one launch boundary fewer per RHS); a batch
+// shape other than the single one takes the prep kernel's tiles.
+int launch_synthesis_tc(sphnse_plan* P, const double* alpha, int pairs) {
     int rc = tc_setup_synthesis(P);
     if (rc) return rc;
-    return launch_prep_tc_batch(P, P->tc.single, alpha);
-}
-
-int launch_synthesis_tc(sphnse_plan* P, int pairs) {
-    int rc = tc_setup_synthesis(P);
-    if (rc) return rc;
-    return launch_synthesis_tc_batch(P, P->tc.single, reinterpret_cast<float*>(P->d_gsyn), 0, pairs);
+    const TcBatch& B = P->tc.single;
+    if (!(B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1)) {
+        if ((rc = launch_prep_tc_batch(P, B, alpha))) return rc;
+        alpha = nullptr;
+    }
+    return launch_synthesis_tc_batch(P, B, reinterpret_cast<float*>(P->d_gsyn), 0, pairs, alpha);
 }
 
 // pieces of every 128-row tile of the [ext row] table: the blocks (m, parity)

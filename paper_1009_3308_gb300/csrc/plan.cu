@@ -151,8 +151,12 @@ int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, doubl
     // four-step ring kernel reads contiguously (its epilogue warps are off the
     // streaming path); the FP32 streaming synthesis keeps the order-major one
     const int pairs = ring4 && tc;
-    if ((rc = tc ? launch_prep_tc(P, alpha) : launch_prep(P, alpha, nullptr, prec))) return rc;
-    if ((rc = tc ? launch_synthesis_tc(P, pairs) : launch_synthesis(P, 3, prec))) return rc;
+    if (tc) {
+        if ((rc = launch_synthesis_tc(P, alpha, pairs))) return rc;   // builds its coefficient tiles
+    } else {
+        if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
+        if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    }
     if (ring4) {
         if ((rc = launch_ring4(P, 1, static_cast<const float*>(P->d_gsyn), 0, static_cast<float*>(P->d_gana), 0,
                                pairs)))
@@ -497,8 +501,12 @@ int sphnse_grid_fields(sphnse_plan* P, const double* alpha, double* zeta, double
     const int prec = P->precision == SPHNSE_FP64 ? SPHNSE_FP64 : SPHNSE_FP32;
     const bool tc = P->precision == SPHNSE_BF16X3 && tc_supported(P);
     int rc;
-    if ((rc = tc ? launch_prep_tc(P, alpha) : launch_prep(P, alpha, nullptr, prec))) return rc;
-    if ((rc = tc ? launch_synthesis_tc(P, 0) : launch_synthesis(P, 3, prec))) return rc;
+    if (tc) {
+        if ((rc = launch_synthesis_tc(P, alpha, 0))) return rc;
+    } else {
+        if ((rc = launch_prep(P, alpha, nullptr, prec))) return rc;
+        if ((rc = launch_synthesis(P, 3, prec))) return rc;
+    }
     if ((rc = launch_transpose(P, P->d_gsyn, P->d_gsyn_r, P->N + 1, P->nlat, 3, prec))) return rc;
     return launch_ring(P, RING_GRID, prec, nullptr, nullptr, zeta, uth, uph);
 }
