@@ -162,12 +162,23 @@ struct HostIO {
 struct TcState {
     void* map_hi = nullptr;      // CUtensorMap of the whole [n_ext][nh] table, global memory
     void* map_lo = nullptr;
-    int4* ana_items = nullptr;   // (tile, first piece, piece count, MMA N)
+    int4* ana_items = nullptr;   // (first row, first piece, piece count, MMA N | first K tile << 16)
     int* ana_off = nullptr;
-    int4* ana_pieces = nullptr;  // (m, parity, first tile row, end tile row)
+    int4* ana_pieces = nullptr;  // (m, parity, first item row, end item row)
     int ana_cta = 0;
     int ana_nf = 0;
     bool ana_ready = false;
+    // the RHS analysis with the finish in its epilogue: order-aligned tiles
+    // in whole order groups per CTA (items and pieces as above, and per item
+    // (group's first row, first order, end order, last item of the group))
+    int4* anf_items = nullptr;
+    int* anf_off = nullptr;
+    int4* anf_pieces = nullptr;
+    int4* anf_og = nullptr;
+    void* anf_map_hi = nullptr;  // 8 maps of the table, boxes of 16 (j + 1) rows
+    void* anf_map_lo = nullptr;
+    int anf_cta = 0;
+    bool anf_ready = false;
     void* smap_hi = nullptr;     // synthesis: tensor maps of the transposed tables
     void* smap_lo = nullptr;
     void* smap_hi_c2 = nullptr;  // the same with boxes of 64 and 32 latitudes (cluster slices)
@@ -306,6 +317,9 @@ bool stream_ok(const sphnse_plan* P, int prec);
 int launch_synthesis_stream(sphnse_plan* P, int nfields, int prec, int pairs = 0);
 bool tc_supported(const sphnse_plan* P);
 int launch_analysis_tc(sphnse_plan* P, int nfields);
+// the RHS's analysis (two product fields) with the recombination and update
+// of the finish step in the epilogue: F = forcing - nu lambda alpha - N
+int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double* forcing, double* out);
 // coefficient prep and synthesis of the plan's own instance (alpha: packed
 // coefficients on the device)
 int launch_synthesis_tc(sphnse_plan* P, const double* alpha, int pairs);

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "f64cvt.h"
+#include "finish.cuh"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -74,15 +75,25 @@ __device__ __forceinline__ uint32_t sw128_chunk(int r, int q) {
 // (hi parts, then lo parts) and the tile rows [s, e); the MMA computes all
 // columns for all rows and the epilogue keeps the columns of each row's piece.
 struct TcAnaArgs {
-    const CUtensorMap* map_hi;   // whole table [n_ext][nh], box 64 x 128
+    const CUtensorMap* map_hi;   // whole table [n_ext][nh], box 64 x 128 (FIN: 8 maps, boxes 64 x 16 (j + 1))
     const CUtensorMap* map_lo;
-    const int4* items;           // (tile, first piece, piece count, N)
+    const int4* items;           // (first table row, first piece, piece count, N | first K tile << 16 | FIN box j << 24)
     const int* item_off;         // per CTA
-    const int4* pieces;          // (m, parity, s, e)
+    const int4* pieces;          // (m, parity, s, e): rows [s, e) of the item's tile
     const float* gana;           // [NF][N+1][nlat] complex float (m-major)
     float* hana;                 // [n_ext][2 NF]
     unsigned* status;
     int N, nh, nlat, nkt, n_ext;
+    // FIN (the RHS recombination and update in the epilogue): per item, its
+    // order group (first table row, first order, end order, last item of the
+    // group), and the finish's operands
+    const int4* og;
+    const double2* alpha;
+    const double2* forcing;
+    double2* out;
+    const float4* finc;
+    double nu, omega_d;
+    int srows;                   // rows of one stage buffer (max(N + 2, 128))
 };
 
 constexpr int TC_ANA_NS = 5;                   // A stages
@@ -99,8 +110,13 @@ constexpr int TC_ANA_BROWS = 32;               // B rows (N) per item at most
 constexpr int TC_ANA_BTILE = TC_ANA_BROWS * TC_TILE_K * 2;   // 4 KB per K tile
 constexpr int TC_ANA_COLS = 128;               // TMEM: 2 buffers x 64 columns
 
-template <int NF>
-__global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
+// FIN: items are order-aligned tiles grouped by order (each CTA takes whole
+// groups); the epilogue keeps a group's projection rows in shared memory and
+// after the group's last tile computes the packed entries of F for its
+// orders (the recombination and diagonal update, Sec. 3), so the RHS needs
+// no separate finish kernel.
+template <int NF, bool FIN = false>
+__global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -116,8 +132,11 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
     uint64_t* b_empty = b_full + 2;
     uint64_t* acc_full = b_full + 4;
     uint64_t* acc_empty = b_full + 6;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 8);
+    uint64_t* st_full = b_full + 8;                               // FIN: an order group's rows staged
+    uint64_t* st_empty = st_full + 2;                             // FIN: its F written, buffer free
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(FIN ? st_empty + 2 : b_full + 8);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);   // FIN: 2 x [srows][4]
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
     const int N = a.N, nh = a.nh, nlat = a.nlat, nkt = a.nkt;
@@ -135,6 +154,10 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             mbar_init(&b_empty[b], 1);
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 128);
+            if constexpr (FIN) {
+                mbar_init(&st_full[b], 128);
+                mbar_init(&st_empty[b], 128);
+            }
         }
         *abort = 0;
         fence_barrier_init();
@@ -157,14 +180,17 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             int it = 0;
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
-                for (int kt = itm.w >> 16; kt < nkt; ++kt, ++it) {
+                // FIN: the box height of the item's rows (16 (bj + 1)) and its map
+                const int bj = FIN ? (itm.w >> 24) & 7 : 0;
+                const uint32_t abytes = uint32_t(2 * TC_TILE_K * 2 * (FIN ? 16 * (bj + 1) : TC_TILE_M));
+                for (int kt = (itm.w >> 16) & 0xFF; kt < nkt; ++kt, ++it) {
                     const int s = it % TC_ANA_NS;
                     if (it >= TC_ANA_NS && !mbar_wait(&a_empty[s], ((it / TC_ANA_NS) - 1) & 1, abort, a.status))
                         continue;
                     if (*abort) continue;
-                    mbar_arrive_expect_tx(&a_full[s], 2 * TC_ATILE);
-                    tma_load_2d(A_hi + s * TC_ATILE, a.map_hi, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
-                    tma_load_2d(A_lo + s * TC_ATILE, a.map_lo, kt * TC_TILE_K, itm.x * TC_TILE_M, &a_full[s], pol);
+                    mbar_arrive_expect_tx(&a_full[s], abytes);
+                    tma_load_2d(A_hi + s * TC_ATILE, a.map_hi + bj, kt * TC_TILE_K, itm.x, &a_full[s], pol);
+                    tma_load_2d(A_lo + s * TC_ATILE, a.map_lo + bj, kt * TC_TILE_K, itm.x, &a_full[s], pol);
                 }
             }
             for (int k = it - TC_ANA_NS; k < it; ++k)
@@ -176,7 +202,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             for (int i = 0; i < nI; ++i) {
                 const int4 itm = a.items[ib + i];
                 const uint32_t idesc = idesc_bf16(TC_TILE_M, itm.w & 0xFFFF);
-                const int kt0 = itm.w >> 16;
+                const int kt0 = (itm.w >> 16) & 0xFF;
                 const int buf = i & 1, use = i >> 1;
                 bool ok = mbar_wait(&b_full[buf], use & 1, abort, a.status);
                 if (i >= 2) ok = mbar_wait(&acc_empty[buf], (use - 1) & 1, abort, a.status) && ok;
@@ -211,7 +237,7 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             const int buf = i & 1;
             if (i >= 2) mbar_wait(&b_empty[buf], ((i >> 1) - 1) & 1, abort, a.status);
             const int4 itm = a.items[ib + i];
-            const int kt0 = itm.w >> 16;
+            const int kt0 = (itm.w >> 16) & 0xFF;
             const int per_piece = (nkt - kt0) * 8 * NF;
             for (int task = ht; task < itm.z * per_piece; task += 128) {
                 const int j = task / per_piece, tl = task % per_piece;
@@ -260,30 +286,75 @@ __global__ void __launch_bounds__(320, 1) k_ana_tc(TcAnaArgs a) {
             fence_proxy_async_smem();
             mbar_arrive(&b_full[buf]);
         }
-    } else {
+    } else if (warp < 10) {
         // epilogue: TMEM lanes of this warp's quarter -> projection rows
+        // (FIN: into the stage buffer of the CTA's g-th order group, g & 1)
         pdl_wait();
         const int quarter = warp & 3;
         const int r = quarter * 32 + lane;               // tile row of this lane
+        int g = 0;
+        bool new_group = true;
         for (int i = 0; i < nI; ++i) {
             const int4 itm = a.items[ib + i];
             const int buf = i & 1;
+            if (FIN && new_group && g >= 2) mbar_wait(&st_empty[g & 1], ((g >> 1) - 1) & 1, abort, a.status);
+            new_group = false;
+            float* sg = stage + (g & 1) * a.srows * 2 * NF;
             const bool ok = mbar_wait(&acc_full[buf], (i >> 1) & 1, abort, a.status);
             tc_fence_after();
-            const int row = itm.x * TC_TILE_M + r;
+            const int row = itm.x + r;
             for (int j = 0; j < itm.z; ++j) {
                 const int4 pc = a.pieces[itm.y + j];
                 if (pc.w <= quarter * 32 || pc.z >= quarter * 32 + 32) continue;   // warp-uniform
                 float v[16];
                 tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * 64 + RP * j), v);
                 if (ok && r >= pc.z && r < pc.w && row < a.n_ext && !*abort) {
+                    if constexpr (FIN) {
+                        const int sr = row - a.og[ib + i].x;
 #pragma unroll
-                    for (int c = 0; c < 2 * NF; ++c)
-                        a.hana[size_t(row) * 2 * NF + c] = v[c] + v[2 * NF + c];
+                        for (int c = 0; c < 2 * NF; ++c) sg[sr * 2 * NF + c] = v[c] + v[2 * NF + c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 2 * NF; ++c)
+                            a.hana[size_t(row) * 2 * NF + c] = v[c] + v[2 * NF + c];
+                    }
                 }
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
+            if (FIN && a.og[ib + i].w) {
+                mbar_arrive(&st_full[g & 1]);   // the group's rows are staged
+                ++g;
+                new_group = true;
+            }
+        }
+    } else if constexpr (FIN) {
+        // finish warps (10 .. 13): F for the orders of each staged group, one
+        // packed entry per thread at a time (the recombination and diagonal
+        // update of finish32_entry), while the epilogue stages the next group
+        pdl_wait();   // alpha and the forcing may be the predecessor's output
+        const int ft = int(threadIdx.x) - 320;
+        int g = 0;
+        for (int i = 0; i < nI; ++i) {
+            const int4 og = a.og[ib + i];
+            if (!og.w) continue;
+            mbar_wait(&st_full[g & 1], (g >> 1) & 1, abort, a.status);
+            const float* sg = stage + (g & 1) * a.srows * 2 * NF;
+            if (!*abort) {
+                for (int m = og.y; m < og.z; ++m) {
+                    const int lo = m > 0 ? m : 1, pk = packed_off(N, m) - lo;
+                    for (int L = lo + ft; L <= N; L += 128) {
+                        const int pi = pk + L;
+                        const float* hL = sg + (ext_row(N, m, L) - og.x) * 2 * NF;
+                        const float* hU = sg + (ext_row(N, m, L + 1) - og.x) * 2 * NF;
+                        const float* hD = L - 1 >= m ? sg + (ext_row(N, m, L - 1) - og.x) * 2 * NF : nullptr;
+                        const double2 f = a.forcing ? a.forcing[pi] : make_double2(0.0, 0.0);
+                        a.out[pi] = finish32_entry(0, L, m, a.finc[pi], hL, hU, hD, a.alpha[pi], f, a.nu, a.omega_d);
+                    }
+                }
+            }
+            mbar_arrive(&st_empty[g & 1]);
+            ++g;
         }
     }
     tc_fence_before();
@@ -1121,11 +1192,11 @@ static const std::vector<float>& tc_chunk_max(sphnse_plan* P) {
 }
 
 // first 64-latitude chunk (from the pole) in which one of the rows
-// tile * 128 + [s, e) of the given pieces reaches TC_SKIP; at most nch - 1
-static int ana_first_chunk(const std::vector<float>& cm, int nch, int tile, const int4* pcs, int np) {
+// row0 + [s, e) of the given pieces reaches TC_SKIP; at most nch - 1
+static int ana_first_chunk(const std::vector<float>& cm, int nch, int row0, const int4* pcs, int np) {
     int c0 = nch - 1;
     for (int j = 0; j < np; ++j)
-        for (int r = tile * TC_TILE_M + pcs[j].z; r < tile * TC_TILE_M + pcs[j].w; ++r)
+        for (int r = row0 + pcs[j].z; r < row0 + pcs[j].w; ++r)
             for (int c = 0; c < c0; ++c)
                 if (cm[size_t(r) * nch + c] >= TC_SKIP) {
                     c0 = c;
@@ -1186,8 +1257,8 @@ int tc_setup_analysis(sphnse_plan* P, int nf) {
             for (size_t j0 = 0; j0 < per[tt].size(); j0 += maxp) {
                 const int np = int(std::min<size_t>(maxp, per[tt].size() - j0));
                 const int ncol = ((4 * nf * np + 15) / 16) * 16;
-                const int kt0 = ana_first_chunk(cm, nch, tt, per[tt].data() + j0, np);
-                items.push_back(make_int4(tt, int(pieces.size()), np, ncol | (kt0 << 16)));
+                const int kt0 = ana_first_chunk(cm, nch, tt * TC_TILE_M, per[tt].data() + j0, np);
+                items.push_back(make_int4(tt * TC_TILE_M, int(pieces.size()), np, ncol | (kt0 << 16)));
                 for (size_t j = j0; j < j0 + np; ++j)
                     T.ana_entries += double(per[tt][j].w - per[tt][j].z) * (nh - std::min(nh, kt0 * TC_TILE_K));
                 int rows = 0;
@@ -1254,6 +1325,142 @@ int launch_analysis_tc(sphnse_plan* P, int nfields) {
     int rc = tc_setup_analysis(P, nfields);
     if (rc) return rc;
     return nfields == 3 ? ana_tc_t<3>(P) : ana_tc_t<2>(P);
+}
+
+// Order groups of the fused analysis: an order of more than 128 table rows
+// alone (its rows in consecutive 128-row tiles), else two consecutive orders
+// whose rows fit one tile (four blocks: the pieces a tile holds).  Each CTA
+// takes whole groups, LPT by the table tiles they read.
+static int tc_setup_analysis_fin(sphnse_plan* P) {
+    auto& T = P->tc;
+    if (T.anf_ready) return SPHNSE_OK;
+    int rc = tc_setup_analysis(P, 2);
+    if (rc) return rc;
+    const int N = P->N, nh = P->nh;
+    const auto& cm = tc_chunk_max(P);
+    const int nch = (nh + TC_TILE_K - 1) / TC_TILE_K;
+    struct Group {
+        std::vector<int4> items, og;
+        std::vector<std::vector<int4>> pcs;
+        double cost = 0;
+    };
+    std::vector<Group> groups;
+    double entries = 0;
+    for (int m = 0; m <= N;) {
+        int m1 = m + 1;
+        if (ext_count(N, m) <= TC_TILE_M && m1 <= N && ext_count(N, m) + ext_count(N, m1) <= TC_TILE_M) ++m1;
+        const int row0 = ext_off(N, m), rows = ext_off(N, m1) - row0;
+        Group g;
+        for (int t0 = 0; t0 < rows; t0 += TC_TILE_M) {
+            const int r0 = row0 + t0, r1 = row0 + std::min(rows, t0 + TC_TILE_M);
+            std::vector<int4> pc;
+            for (int mm = m; mm < m1; ++mm)
+                for (int par = 0; par < 2; ++par) {
+                    const int ne = ext_even(N, mm);
+                    const int b0 = ext_off(N, mm) + (par ? ne : 0), b1 = b0 + (par ? ext_odd(N, mm) : ne);
+                    const int s0 = std::max(b0, r0), s1 = std::min(b1, r1);
+                    if (s0 < s1) pc.push_back(make_int4(mm, par, s0 - r0, s1 - r0));
+                }
+            const int np = int(pc.size());
+            const int ncol = ((8 * np + 15) / 16) * 16;
+            const int kt0 = ana_first_chunk(cm, nch, r0, pc.data(), np);
+            for (const int4& q : pc) entries += double(q.w - q.z) * (nh - std::min(nh, kt0 * TC_TILE_K));
+            const int bj = (r1 - r0 + 15) / 16 - 1;
+            g.items.push_back(make_int4(r0, 0, np, ncol | (kt0 << 16) | (bj << 24)));
+            g.og.push_back(make_int4(row0, m, m1, r1 == row0 + rows ? 1 : 0));
+            g.pcs.push_back(pc);
+            g.cost += (TC_TILE_M + 24 * np) * double(nch - kt0) / nch;
+        }
+        groups.push_back(std::move(g));
+        m = m1;
+    }
+    std::vector<int> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return groups[x].cost > groups[y].cost; });
+    const int G = std::min<int>(P->n_cta, int(groups.size()));
+    std::vector<std::vector<int>> bins(G);
+    std::vector<double> load(G, 0.0);
+    for (int idx : order) {
+        const int b = int(std::min_element(load.begin(), load.end()) - load.begin());
+        bins[b].push_back(idx);
+        load[b] += groups[idx].cost;
+    }
+    // maps with boxes of 16 .. 128 rows: a group's last tile reads its own rows
+    // rounded up to 16, not a full tile of the next group's
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return SPHNSE_E_UNSUPPORTED;
+    CUtensorMap mh[8], ml[8];
+    {
+        const Tables& t = P->tab[SPHNSE_BF16X3];
+        const cuuint64_t dims[2] = {cuuint64_t(nh), cuuint64_t(P->n_ext)};
+        const cuuint64_t strides[1] = {cuuint64_t(nh) * 2};
+        const cuuint32_t es[2] = {1, 1};
+        for (int j = 0; j < 8; ++j) {
+            const cuuint32_t box[2] = {TC_TILE_K, cuuint32_t(16 * (j + 1))};
+            for (int lo = 0; lo < 2; ++lo) {
+                CUresult r = enc(lo ? &ml[j] : &mh[j], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                 const_cast<void*>(lo ? t.syn_lo : t.syn), dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) return SPHNSE_E_CUDA;
+            }
+        }
+    }
+    std::vector<int4> items, og, pieces;
+    std::vector<int> off(1, 0);
+    for (auto& bi : bins) {
+        for (int gi : bi) {
+            const Group& g = groups[gi];
+            for (size_t k = 0; k < g.items.size(); ++k) {
+                int4 it = g.items[k];
+                it.y = int(pieces.size());
+                pieces.insert(pieces.end(), g.pcs[k].begin(), g.pcs[k].end());
+                items.push_back(it);
+                og.push_back(g.og[k]);
+            }
+        }
+        off.push_back(int(items.size()));
+    }
+    if (cudaMalloc(&T.anf_map_hi, sizeof(mh)) != cudaSuccess || cudaMalloc(&T.anf_map_lo, sizeof(ml)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.anf_items), items.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.anf_og), og.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.anf_off), off.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&T.anf_pieces), pieces.size() * sizeof(int4)) != cudaSuccess)
+        return SPHNSE_E_NOMEM;
+    cudaMemcpy(T.anf_map_hi, mh, sizeof(mh), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.anf_map_lo, ml, sizeof(ml), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.anf_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.anf_og, og.data(), og.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.anf_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.anf_pieces, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    T.anf_cta = G;
+    T.ana_entries = entries;
+    T.anf_ready = true;
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double* forcing, double* out) {
+    int rc = tc_setup_analysis_fin(P);
+    if (rc) return rc;
+    const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
+    // stages, B tiles, barriers (256 B) and two stage buffers of an order
+    // group's rows (one order of N + 2 rows, or two within a 128-row tile)
+    const int srows = std::max(P->N + 2, TC_TILE_M);
+    const size_t sm = 1024 + 2 * size_t(TC_ANA_NS) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256 +
+                      2 * size_t(srows) * 4 * sizeof(float);
+    if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
+    allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_tc<2, true>), sm);
+    TcAnaArgs a{reinterpret_cast<const CUtensorMap*>(P->tc.anf_map_hi),
+                reinterpret_cast<const CUtensorMap*>(P->tc.anf_map_lo), P->tc.anf_items, P->tc.anf_off,
+                P->tc.anf_pieces,
+                reinterpret_cast<const float*>(P->d_gana), nullptr, P->d_status,
+                P->N, P->nh, P->nlat, nkt, P->n_ext,
+                P->tc.anf_og, reinterpret_cast<const double2*>(alpha), reinterpret_cast<const double2*>(forcing),
+                reinterpret_cast<double2*>(out), P->d_finc32, P->nu, P->coriolis_split ? P->Omega : 0.0, srows};
+    stage_begin(P, SPHNSE_STAGE_ANALYSIS);
+    const cudaError_t e = launch_pdl(k_ana_tc<2, true>, dim3(P->tc.anf_cta), dim3(448), sm, P->stream, a);
+    stage_end(P, SPHNSE_STAGE_ANALYSIS);
+    return check_cuda(e);
 }
 
 // Transposed, padded bf16 hi/lo tables for the synthesis (block (m, parity)
@@ -1696,7 +1903,8 @@ int launch_analysis_tc_batch(sphnse_plan* P, const TcBatchA& B, const float* gan
 
 void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
-    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.smap_hi, T.smap_lo, T.tsyn_hi,
+    void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.anf_items, T.anf_off, T.anf_pieces,
+                    T.anf_og, T.anf_map_hi, T.anf_map_lo, T.smap_hi, T.smap_lo, T.tsyn_hi,
                     T.tsyn_lo, T.tile_off, T.tile_info, T.syn_kt0, T.smap_hi_c2, T.smap_lo_c2, T.smap_hi_c4,
                     T.smap_lo_c4};
     for (void* p : ptrs)

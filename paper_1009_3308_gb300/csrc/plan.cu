@@ -166,6 +166,12 @@ int rhs_device(sphnse_plan* P, const double* alpha, const double* forcing, doubl
         if ((rc = launch_ring(P, RING_RHS, prec, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
         if ((rc = launch_transpose(P, P->d_gana_r, P->d_gana, P->nlat, P->N + 1, 2, prec))) return rc;
     }
+    if (tc) {
+        // the finish step runs in the analysis epilogue where its shared
+        // memory fits
+        rc = launch_analysis_finish_tc(P, alpha, forcing, out);
+        if (rc != SPHNSE_E_UNSUPPORTED) return rc;
+    }
     if ((rc = tc ? launch_analysis_tc(P, 2) : launch_analysis(P, 2, prec))) return rc;
     return launch_finish(P, 0, prec, alpha, forcing, out);
 }
