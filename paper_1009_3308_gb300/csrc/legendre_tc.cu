@@ -93,10 +93,11 @@ struct TcAnaArgs {
     double2* out;
     const float4* finc;
     double nu, omega_d;
-    int srows;                   // rows of one stage buffer (max(N + 2, 128))
+    int srows;                   // rows of one stage buffer (max(2 (N + 2), 128))
 };
 
 constexpr int TC_ANA_NS = 5;                   // A stages
+constexpr int TC_ANA_NS_FIN = 4;               // A stages of the RHS form (its shared memory holds two stage buffers)
 
 // Table tiles whose entries are all below TC_SKIP in magnitude are not read:
 // near the poles Pt_K^m decays like sin(theta)^m below its turning point
@@ -122,13 +123,14 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~uintptr_t(1023));
     constexpr int RP = 4 * NF;                                    // B rows per piece
+    constexpr int ANS = FIN ? TC_ANA_NS_FIN : TC_ANA_NS;          // A stages
     unsigned char* A_hi = smem;                                   // NS x 16 KB
-    unsigned char* A_lo = A_hi + TC_ANA_NS * TC_ATILE;            // NS x 16 KB
-    unsigned char* Bt = A_lo + TC_ANA_NS * TC_ATILE;              // 2 bufs x nkt x 4 KB
+    unsigned char* A_lo = A_hi + ANS * TC_ATILE;            // NS x 16 KB
+    unsigned char* Bt = A_lo + ANS * TC_ATILE;              // 2 bufs x nkt x 4 KB
     uint64_t* bars = reinterpret_cast<uint64_t*>(Bt + 2 * a.nkt * TC_ANA_BTILE);
     uint64_t* a_full = bars;
-    uint64_t* a_empty = bars + TC_ANA_NS;
-    uint64_t* b_full = bars + 2 * TC_ANA_NS;
+    uint64_t* a_empty = bars + ANS;
+    uint64_t* b_full = bars + 2 * ANS;
     uint64_t* b_empty = b_full + 2;
     uint64_t* acc_full = b_full + 4;
     uint64_t* acc_empty = b_full + 6;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
         reinterpret_cast<uint4*>(Bt)[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async_smem();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_ANA_NS; ++s) {
+        for (int s = 0; s < ANS; ++s) {
             mbar_init(&a_full[s], 1);
             mbar_init(&a_empty[s], 1);
         }
@@ -184,8 +186,8 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
                 const int bj = FIN ? (itm.w >> 24) & 7 : 0;
                 const uint32_t abytes = uint32_t(2 * TC_TILE_K * 2 * (FIN ? 16 * (bj + 1) : TC_TILE_M));
                 for (int kt = (itm.w >> 16) & 0xFF; kt < nkt; ++kt, ++it) {
-                    const int s = it % TC_ANA_NS;
-                    if (it >= TC_ANA_NS && !mbar_wait(&a_empty[s], ((it / TC_ANA_NS) - 1) & 1, abort, a.status))
+                    const int s = it % ANS;
+                    if (it >= ANS && !mbar_wait(&a_empty[s], ((it / ANS) - 1) & 1, abort, a.status))
                         continue;
                     if (*abort) continue;
                     mbar_arrive_expect_tx(&a_full[s], abytes);
@@ -193,8 +195,8 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
                     tma_load_2d(A_lo + s * TC_ATILE, a.map_lo + bj, kt * TC_TILE_K, itm.x, &a_full[s], pol);
                 }
             }
-            for (int k = it - TC_ANA_NS; k < it; ++k)
-                if (k >= 0) mbar_wait(&a_full[k % TC_ANA_NS], (k / TC_ANA_NS) & 1, abort, a.status);
+            for (int k = it - ANS; k < it; ++k)
+                if (k >= 0) mbar_wait(&a_full[k % ANS], (k / ANS) & 1, abort, a.status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -209,8 +211,8 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
                 tc_fence_after();
                 const uint32_t d = tmem + uint32_t(buf * 64);
                 for (int kt = kt0; kt < nkt; ++kt, ++it) {
-                    const int s = it % TC_ANA_NS;
-                    const bool okA = mbar_wait(&a_full[s], (it / TC_ANA_NS) & 1, abort, a.status);
+                    const int s = it % ANS;
+                    const bool okA = mbar_wait(&a_full[s], (it / ANS) & 1, abort, a.status);
                     tc_fence_after();
                     if (ok && okA && !*abort) {
                         const unsigned char* bt = Bt + (buf * nkt + kt) * TC_ANA_BTILE;
@@ -1327,9 +1329,9 @@ int launch_analysis_tc(sphnse_plan* P, int nfields) {
     return nfields == 3 ? ana_tc_t<3>(P) : ana_tc_t<2>(P);
 }
 
-// Order groups of the fused analysis: an order of more than 128 table rows
-// alone (its rows in consecutive 128-row tiles), else two consecutive orders
-// whose rows fit one tile (four blocks: the pieces a tile holds).  Each CTA
+// Order groups of the fused analysis: consecutive orders whose rows (at
+// most two orders' worth) go through consecutive 128-row tiles, each tile
+// with at most two orders (four blocks: the pieces a tile holds).  Each CTA
 // takes whole groups, LPT by the table tiles they read.
 static int tc_setup_analysis_fin(sphnse_plan* P) {
     auto& T = P->tc;
@@ -1346,9 +1348,28 @@ static int tc_setup_analysis_fin(sphnse_plan* P) {
     };
     std::vector<Group> groups;
     double entries = 0;
+    // a group takes the next order while its rows fit a stage buffer, every
+    // 128-row tile still holds at most two orders (four blocks), and the
+    // merge saves a tile
+    const int cap = std::max(2 * (N + 2), TC_TILE_M);
+    auto ntiles = [](int rows) { return (rows + TC_TILE_M - 1) / TC_TILE_M; };
+    auto two_per_tile = [&](int m, int m1) {
+        const int r0 = ext_off(N, m), r1 = ext_off(N, m1);
+        for (int t = r0; t < r1; t += TC_TILE_M) {
+            const int te = std::min(r1, t + TC_TILE_M);
+            int k = 0;
+            for (int mm = m; mm < m1; ++mm)
+                if (ext_off(N, mm) < te && ext_off(N, mm + 1) > t) ++k;
+            if (k > 2) return false;
+        }
+        return true;
+    };
     for (int m = 0; m <= N;) {
         int m1 = m + 1;
-        if (ext_count(N, m) <= TC_TILE_M && m1 <= N && ext_count(N, m) + ext_count(N, m1) <= TC_TILE_M) ++m1;
+        while (m1 <= N && ext_off(N, m1 + 1) - ext_off(N, m) <= cap && two_per_tile(m, m1 + 1) &&
+               ntiles(ext_off(N, m1 + 1) - ext_off(N, m)) <
+                   ntiles(ext_off(N, m1) - ext_off(N, m)) + ntiles(ext_count(N, m1)))
+            ++m1;
         const int row0 = ext_off(N, m), rows = ext_off(N, m1) - row0;
         Group g;
         for (int t0 = 0; t0 < rows; t0 += TC_TILE_M) {
@@ -1444,9 +1465,9 @@ int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double*
     if (rc) return rc;
     const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
     // stages, B tiles, barriers (256 B) and two stage buffers of an order
-    // group's rows (one order of N + 2 rows, or two within a 128-row tile)
-    const int srows = std::max(P->N + 2, TC_TILE_M);
-    const size_t sm = 1024 + 2 * size_t(TC_ANA_NS) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256 +
+    // group's rows (at most two orders, 2 (N + 2) rows)
+    const int srows = std::max(2 * (P->N + 2), TC_TILE_M);
+    const size_t sm = 1024 + 2 * size_t(TC_ANA_NS_FIN) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256 +
                       2 * size_t(srows) * 4 * sizeof(float);
     if (sm > 227 * 1024) return SPHNSE_E_UNSUPPORTED;
     allow_dynamic_smem(reinterpret_cast<const void*>(k_ana_tc<2, true>), sm);
