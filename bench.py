@@ -673,9 +673,10 @@ def main():
                 "traffic": ncu_traffic(f"{dom}:{prec}:L511")}
 
     # end to end through the C ABI with host buffers (sphnse_rhs_host): every
-    # step uploads its alpha from pinned memory and downloads its F; the host
-    # reads each step's F one step later (host_wait), so that step k + 1's
-    # copies overlap step k's RHS
+    # step uploads its alpha from pinned memory and its F reaches pinned
+    # memory (written there by the analysis); the host reads each step's F
+    # one step later (host_wait), so that step k + 1's transfers overlap step
+    # k's RHS
     pin_in = [torch.from_numpy(w["alpha0"]).pin_memory() for _ in range(2)]
     pin_out = [torch.empty_like(pin_in[0]).pin_memory() for _ in range(2)]
     for i in range(4):
@@ -696,7 +697,7 @@ def main():
     el = max_over_ranks(world, el)
     e2e = {"value": replica_rate(world, k_e2e, el), "unit": UNIT, "h2d_bytes_per_step": pin_in[0].numel() * 16,
            "d2h_bytes_per_step": pin_out[0].numel() * 16, "steps": k_e2e,
-           "api": "sphnse_rhs_host (pinned host buffers, copies overlapped with the previous step's RHS)",
+           "api": "sphnse_rhs_host (pinned host buffers: alpha copied up before the step's kernels, F written by the analysis into the page-locked output; both overlap the previous step's RHS)",
            "finite": bool(np.isfinite(chk))}
 
     extras = {}

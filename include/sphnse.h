@@ -161,18 +161,24 @@ int sphnse_rhs(sphnse_plan* plan, double t, const double* alpha, const double* f
 
 /* F(t, alpha) of Eq. (ode) from HOST arrays, pipelined across calls.  Each
  * call copies alpha_h (and forcing_h, nullable) into one of two plan-owned
- * device staging slots on an upload stream, evaluates F on the plan's stream
- * and copies it to out_h on a download stream, and returns without waiting
- * (*ticket, nullable, numbers the call from 0).  Call k + 1's upload overlaps
- * call k's RHS and call k's download overlaps call k + 1's RHS.  The host
- * arrays (n_coeff complex128 each; page-locked for the copies to overlap)
- * must stay valid, and alpha_h / forcing_h unmodified, until
+ * device staging slots on an upload stream, evaluates F on the plan's
+ * stream, and returns without waiting for F (*ticket, nullable, numbers the
+ * call from 0).  F reaches out_h in one of two ways:
+ * - out_h page-locked and mapped, BF16X3 plan on the fused tensor-core RHS:
+ *   the call waits for its upload before queueing the RHS, and the analysis
+ *   writes F into out_h itself (the plan's stream then holds only the RHS
+ *   kernels, so consecutive calls overlap);
+ * - otherwise a copy on a download stream; call k + 1's upload overlaps call
+ *   k's RHS and call k's download overlaps call k + 1's RHS.
+ * The host arrays (n_coeff complex128 each; page-locked for the transfers
+ * to overlap) must stay valid, and alpha_h / forcing_h unmodified, until
  * sphnse_host_wait(plan, ticket) has returned; out_h is valid from then on. */
 int sphnse_rhs_host(sphnse_plan* plan, double t, const double* alpha_h, const double* forcing_h,
                     double* out_h, long long* ticket);
 
-/* Block until call `ticket` of sphnse_rhs_host has copied F to the host
- * (E_ARG for a ticket not yet issued). */
+/* Block until call `ticket` of sphnse_rhs_host has delivered F to the host
+ * (E_ARG for a ticket not yet issued; E_TIMEOUT if a direct-output call has
+ * not reported completion within 30 s). */
 int sphnse_host_wait(sphnse_plan* plan, long long ticket);
 
 /* Grid values of zeta = xhat.Curl_n u (Eq. (vort_app)), u_theta and u_phi

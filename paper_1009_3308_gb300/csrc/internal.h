@@ -156,6 +156,14 @@ struct HostIO {
     cudaStream_t up = nullptr, down = nullptr;
     long long calls = 0;
     bool ready = false;
+    // direct output (a page-locked, device-mapped out_h on the fused
+    // tensor-core RHS): the analysis writes F into out_h, and its last CTA
+    // writes the call's ticket + 1 to *flag (mapped host memory) after every
+    // CTA's writes of F
+    volatile unsigned long long* flag = nullptr;
+    unsigned long long* dflag = nullptr;   // device address of flag
+    unsigned* dcnt = nullptr;              // CTAs of the running analysis done
+    long long direct[2] = {-1, -1};        // the last direct-output call of each slot
 };
 
 // tcgen05 path state (tensor maps and item schedules, built on first use)
@@ -263,6 +271,10 @@ struct sphnse_plan {
     unsigned timing = 0;         // bit mask of timed stages
     int timing_period = 1;       // record every timing_period-th launch of a timed stage
     int ring_threads = 0;        // four-step ring kernel: 0 chooses, 128 or 256 threads per G rings
+    // set for one direct-output sphnse_rhs_host call: the RHS analysis reports completion
+    unsigned* done_cnt = nullptr;
+    unsigned long long* done_flag = nullptr;
+    unsigned long long done_ticket = 0;
     int nsm = 1;                 // SMs of the plan's device
     long stage_calls[8] = {};    // launches seen per stage while timed
     bool stage_rec[8] = {};      // the current launch of the stage is recorded
@@ -320,6 +332,9 @@ int launch_analysis_tc(sphnse_plan* P, int nfields);
 // the RHS's analysis (two product fields) with the recombination and update
 // of the finish step in the epilogue: F = forcing - nu lambda alpha - N
 int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double* forcing, double* out);
+// true when the RHS runs as the three fused tensor-core kernels (the
+// synthesis builds its coefficient tiles, the analysis runs the finish)
+bool tc_rhs_fused(sphnse_plan* P);
 // coefficient prep and synthesis of the plan's own instance (alpha: packed
 // coefficients on the device)
 int launch_synthesis_tc(sphnse_plan* P, const double* alpha, int pairs);

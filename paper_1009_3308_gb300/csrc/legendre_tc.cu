@@ -94,6 +94,10 @@ struct TcAnaArgs {
     const float4* finc;
     double nu, omega_d;
     int srows;                   // rows of one stage buffer (max(2 (N + 2), 128))
+    // FIN, direct-output calls: CTAs done, and the mapped host flag the last one sets to done_ticket
+    unsigned* done_cnt;
+    unsigned long long* done_flag;
+    unsigned long long done_ticket;
 };
 
 constexpr int TC_ANA_NS = 5;                   // A stages
@@ -359,11 +363,22 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
             ++g;
         }
     }
+    // direct-output calls: every thread's writes of F reach the system
+    // before the CTA counts itself done
+    if (FIN && a.done_flag) __threadfence_system();
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, TC_ANA_COLS);
+    }
+    if constexpr (FIN) {
+        // the last CTA to finish reports the call complete in mapped host memory
+        if (a.done_flag && threadIdx.x == 0 && atomicAdd(a.done_cnt, 1u) == gridDim.x - 1) {
+            *a.done_cnt = 0u;
+            __threadfence_system();
+            *reinterpret_cast<volatile unsigned long long*>(a.done_flag) = a.done_ticket;
+        }
     }
 }
 
@@ -1460,6 +1475,18 @@ static int tc_setup_analysis_fin(sphnse_plan* P) {
     return check_cuda(cudaGetLastError());
 }
 
+bool tc_rhs_fused(sphnse_plan* P) {
+    if (P->precision != SPHNSE_BF16X3 || !tc_supported(P) || !ring4_ok(P)) return false;
+    if (tc_setup_synthesis(P) || tc_setup_analysis_fin(P)) return false;
+    const TcBatch& B = P->tc.single;
+    if (!(B.nb == 1 && B.ng == 1 && B.brows == 16 && B.ns == 6 && B.cs == 1)) return false;
+    const int nkt = (P->nh + TC_TILE_K - 1) / TC_TILE_K;
+    const int srows = std::max(2 * (P->N + 2), TC_TILE_M);
+    const size_t sm = 1024 + 2 * size_t(TC_ANA_NS_FIN) * TC_ATILE + 2 * size_t(nkt) * TC_ANA_BTILE + 256 +
+                      2 * size_t(srows) * 4 * sizeof(float);
+    return sm <= 227 * 1024;
+}
+
 int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double* forcing, double* out) {
     int rc = tc_setup_analysis_fin(P);
     if (rc) return rc;
@@ -1477,7 +1504,8 @@ int launch_analysis_finish_tc(sphnse_plan* P, const double* alpha, const double*
                 reinterpret_cast<const float*>(P->d_gana), nullptr, P->d_status,
                 P->N, P->nh, P->nlat, nkt, P->n_ext,
                 P->tc.anf_og, reinterpret_cast<const double2*>(alpha), reinterpret_cast<const double2*>(forcing),
-                reinterpret_cast<double2*>(out), P->d_finc32, P->nu, P->coriolis_split ? P->Omega : 0.0, srows};
+                reinterpret_cast<double2*>(out), P->d_finc32, P->nu, P->coriolis_split ? P->Omega : 0.0, srows,
+                P->done_cnt, P->done_flag, P->done_ticket};
     stage_begin(P, SPHNSE_STAGE_ANALYSIS);
     const cudaError_t e = launch_pdl(k_ana_tc<2, true>, dim3(P->tc.anf_cta), dim3(448), sm, P->stream, a);
     stage_end(P, SPHNSE_STAGE_ANALYSIS);
