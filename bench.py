@@ -118,6 +118,14 @@ def algorithmic(stage, L, nlat, prec, entries=None):
     tb = {"fp64": 8, "fp32": 4, "bf16x3": 4}[prec]     # table bytes per entry (hi+lo for bf16)
     vb = 8 if prec == "fp64" else 4                     # intermediate real size
     g = nlat * (L + 1) * 2 * vb                         # one complex [nlat][L+1] field
+    nc = (L + 1) * (L + 2) // 2 - 1                     # packed coefficients (complex128 state)
+    if prec == "bf16x3":
+        # the tensor-core RHS: the synthesis reads alpha itself (its coefficient
+        # tiles are built in the kernel), the analysis reads alpha and writes F
+        if stage == "synthesis":
+            return E * tb + nc * 16 + 3 * g, 12 * E
+        if stage == "analysis":
+            return E * tb + 2 * g + 2 * nc * 16, 8 * E
     if stage == "synthesis":
         return E * tb + n_ext * 6 * vb + 3 * g, 12 * E
     if stage == "analysis":
