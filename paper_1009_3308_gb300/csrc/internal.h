@@ -95,8 +95,9 @@ struct TcBatch {
     int nb = 0, ng = 0, ngroups = 0, brows = 0, ns = 0, ncta = 0;
     int cs = 1;                        // CTAs per cluster sharing every table tile (multicast)
     unsigned char* btiles = nullptr;   // [group][tile][brows][64] bf16, swizzled
-    int4* items = nullptr;
-    int* off = nullptr;
+    int4* items = nullptr;             // (m, latitude tile, group, first K tiles) per CTA at c * istride
+    int* cnt = nullptr;                // items per CTA
+    int istride = 0;
 };
 
 // Batched tcgen05 analysis (NF = 2) over nb instances of one truncation:
@@ -203,10 +204,8 @@ struct TcState {
     size_t tsyn_bytes = 0;
     bool syn_ready = false;
     // negligible table tiles: first significant synthesis K tile per (block,
-    // latitude tile) (the block's tile count if none), and max |Pt| per
-    // (table row, 64-latitude chunk)
-    int* syn_kt0 = nullptr;
-    int syn_nmt = 0;
+    // latitude tile) (the block's tile count if none), [2 (N + 1)][latitude
+    // tiles], and max |Pt| per (table row, 64-latitude chunk)
     double syn_entries = 0, ana_entries = 0;   // table entries one launch reads (skip rule applied)
     std::vector<int> syn_kt0_host;
     std::vector<float> chunk_max;

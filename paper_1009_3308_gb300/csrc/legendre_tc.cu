@@ -754,8 +754,9 @@ __device__ __forceinline__ void prep_words(const double2* __restrict__ alpha, co
 struct TcSynArgs {
     const CUtensorMap* map_hi;   // per (m, parity) block of the transposed tables
     const CUtensorMap* map_lo;
-    const int4* items;           // (m, latitude tile, instance group, 0) per CTA (LPT)
-    const int* item_off;
+    const int4* items;           // (m, latitude tile, instance group, first K tile of the even | odd
+                                 // block << 16), CTA c's list (LPT) at c * istride
+    const int* item_cnt;         // items of every CTA
     const unsigned char* btiles; // [group][tile][brows][64] bf16, 128-byte swizzle (k_prep_tc)
     const int* tile_off;         // first tile of block b = 2 m + parity
     float* gsyn;                 // instance i writes gsyn + i * sgs complex entries
@@ -764,8 +765,7 @@ struct TcSynArgs {
     int N, nh, nlat, nblk, pairs;
     int ng, nb, brows, ntiles, ns;   // instances per group, instances, B rows (= MMA N), tiles, stages
     size_t sgs;
-    const int* kt0;              // first K tile per (block, latitude tile): [2 (N+1)][nmt]
-    int nmt;
+    int istride;                 // item slots per CTA (>= its item count)
     // clusters of CS > 1 CTAs: maps of the same blocks with boxes of 128 / CS latitudes
     const CUtensorMap* map_hi_cs;
     const CUtensorMap* map_lo_cs;
@@ -853,18 +853,11 @@ __global__ void __launch_bounds__(SINGLE ? 192 + 32 * TC_SYN_BUILDERS : 192, 1) 
         *abort = 0;
         fence_barrier_init();
     }
-    const int ib = a.item_off[blockIdx.x / CS], nI = a.item_off[blockIdx.x / CS + 1] - ib;
-    for (int j = threadIdx.x; j < nI && j < TC_SYN_SMITEMS; j += blockDim.x) {
-        const int4 itm = a.items[ib + j];
-        const int e = a.kt0[(2 * itm.x) * a.nmt + itm.y], o = a.kt0[(2 * itm.x + 1) * a.nmt + itm.y];
-        s_items[j] = make_int4(itm.x, itm.y, itm.z, e | (o << 16));
-    }
-    auto item_meta = [&](int i) -> int4 {
-        if (i < TC_SYN_SMITEMS) return s_items[i];
-        const int4 itm = a.items[ib + i];
-        const int e = a.kt0[(2 * itm.x) * a.nmt + itm.y], o = a.kt0[(2 * itm.x + 1) * a.nmt + itm.y];
-        return make_int4(itm.x, itm.y, itm.z, e | (o << 16));
-    };
+    // the lists sit at a fixed stride, so the item loads do not wait on
+    // the count (a kernel's first table request waits on this chain)
+    const int ib = (blockIdx.x / CS) * a.istride, nI = a.item_cnt[blockIdx.x / CS];
+    for (int j = threadIdx.x; j < a.istride && j < TC_SYN_SMITEMS; j += blockDim.x) s_items[j] = a.items[ib + j];
+    auto item_meta = [&](int i) -> int4 { return i < TC_SYN_SMITEMS ? s_items[i] : a.items[ib + i]; };
     if (warp == 1) {
         tmem_alloc(tmem_slot, tcols);
         tmem_relinquish();
@@ -881,7 +874,10 @@ __global__ void __launch_bounds__(SINGLE ? 192 + 32 * TC_SYN_BUILDERS : 192, 1) 
     if (warp == 0 && SINGLE) {
         if (lane == 0) {
             // the table does not depend on the predecessor (no wait); the
-            // builder warps write every stage's coefficient tile
+            // builder warps write every stage's coefficient tile. Only the
+            // first stage is requested before its data lands: the builders'
+            // first coefficient loads would otherwise queue behind every
+            // CTA's full pipeline of table requests
             const uint64_t pol = policy_evict_first();
             int it = 0;
             for (int i = 0; i < nI; ++i) {
@@ -892,6 +888,7 @@ __global__ void __launch_bounds__(SINGLE ? 192 + 32 * TC_SYN_BUILDERS : 192, 1) 
                     const int tw = syn_tailw(N, m, par);
                     for (int kt = ((itm.w >> (16 * par)) & 0xFFFF); kt < nkt; ++kt, ++it) {
                         const int s = it % ns;
+                        if (it == 1 && !mbar_wait(&a_full[0], 0, abort, a.status)) continue;
                         if (it >= ns && !mbar_wait(&a_empty[s], ((it / ns) - 1) & 1, abort, a.status)) continue;
                         if (*abort) continue;
                         const bool last = kt == nkt - 1;
@@ -1627,11 +1624,7 @@ int tc_setup_synthesis(sphnse_plan* P) {
                     T.syn_entries += double(rows) * std::min(TC_TILE_K, n - kt * TC_TILE_K);
             }
         }
-        if (cudaMalloc(reinterpret_cast<void**>(&T.syn_kt0), k0.size() * sizeof(int)) != cudaSuccess)
-            return SPHNSE_E_NOMEM;
-        cudaMemcpy(T.syn_kt0, k0.data(), k0.size() * sizeof(int), cudaMemcpyHostToDevice);
-        T.syn_nmt = nmt;
-        T.syn_kt0_host = k0;
+        T.syn_kt0_host = k0;   // the item lists carry it (tc_batch_init)
     }
     T.tsyn_bytes = 2 * total * 2;
     T.syn_ready = true;
@@ -1683,11 +1676,11 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax, int 
         const int ngi = std::max(0, std::min(T.ng, nb - gq * cs * T.ng));
         for (int m = 0; m <= N; ++m)
             for (int mt = 0; mt < nmt; ++mt) {
-                its.push_back(make_int4(m, mt, gq, 0));
-                // streamed stages (A and B bytes) plus a fixed cost per item and the epilogue of the group
                 const auto& k0 = P->tc.syn_kt0_host;
-                const int nst = syn_nkt(N, m, 0) - k0[size_t(2 * m) * nmt + mt] + syn_nkt(N, m, 1) -
-                                k0[size_t(2 * m + 1) * nmt + mt];
+                const int k0e = k0[size_t(2 * m) * nmt + mt], k0o = k0[size_t(2 * m + 1) * nmt + mt];
+                its.push_back(make_int4(m, mt, gq, k0e | (k0o << 16)));
+                // streamed stages (A and B bytes) plus a fixed cost per item and the epilogue of the group
+                const int nst = syn_nkt(N, m, 0) - k0e + syn_nkt(N, m, 1) - k0o;
                 cost.push_back(nst * (1.0 + T.brows / 256.0) + 1.0 + 0.1 * (ngi - 1));
             }
     }
@@ -1711,26 +1704,30 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax, int 
         bins[bb].push_back(its[idx]);
         load[bb] += cost[idx];
     }
-    std::vector<int4> flat;
-    std::vector<int> offs(1, 0);
-    for (auto& bi : bins) {
-        flat.insert(flat.end(), bi.begin(), bi.end());
-        offs.push_back(int(flat.size()));
+    // every CTA's list at a fixed stride (padded with unused slots)
+    size_t stride = 1;
+    for (auto& bi : bins) stride = std::max(stride, bi.size());
+    std::vector<int4> flat(size_t(G) * stride, make_int4(0, 0, 0, 0));
+    std::vector<int> cnt(G);
+    for (int bb = 0; bb < G; ++bb) {
+        std::copy(bins[bb].begin(), bins[bb].end(), flat.begin() + size_t(bb) * stride);
+        cnt[bb] = int(bins[bb].size());
     }
     if (cudaMalloc(reinterpret_cast<void**>(&T.items), flat.size() * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&T.off), offs.size() * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(reinterpret_cast<void**>(&T.cnt), cnt.size() * sizeof(int)) != cudaSuccess) {
         tc_batch_free(&T);
         return SPHNSE_E_NOMEM;
     }
     cudaMemcpy(T.items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    cudaMemcpy(T.off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(T.cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    T.istride = int(stride);
     T.ncta = G * cs;
     *B = T;
     return check_cuda(cudaGetLastError());
 }
 
 void tc_batch_free(TcBatch* B) {
-    for (void* q : {static_cast<void*>(B->btiles), static_cast<void*>(B->items), static_cast<void*>(B->off)})
+    for (void* q : {static_cast<void*>(B->btiles), static_cast<void*>(B->items), static_cast<void*>(B->cnt)})
         if (q) cudaFree(q);
     *B = TcBatch();
 }
@@ -1795,9 +1792,9 @@ int launch_synthesis_tc_batch(sphnse_plan* P, const TcBatch& B, float* gsyn, siz
     allow_dynamic_smem(reinterpret_cast<const void*>(kern), sm);
     const auto& T = P->tc;
     TcSynArgs a{reinterpret_cast<const CUtensorMap*>(T.smap_hi), reinterpret_cast<const CUtensorMap*>(T.smap_lo),
-                B.items, B.off, B.btiles, T.tile_off, gsyn,
+                B.items, B.cnt, B.btiles, T.tile_off, gsyn,
                 P->d_isin32, P->d_status, P->N, P->nh, P->nlat, 2 * (P->N + 1), pairs,
-                B.ng, B.nb, B.brows, T.ntiles, B.ns, sg_floats / 2, T.syn_kt0, T.syn_nmt,
+                B.ng, B.nb, B.brows, T.ntiles, B.ns, sg_floats / 2, B.istride,
                 reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_hi_c2 : T.smap_hi_c4),
                 reinterpret_cast<const CUtensorMap*>(B.cs == 2 ? T.smap_lo_c2 : T.smap_lo_c4),
                 reinterpret_cast<const double2*>(alpha), P->d_prepc32};
@@ -1954,7 +1951,7 @@ void tc_free(sphnse_plan* P) {
     auto& T = P->tc;
     void* ptrs[] = {T.map_hi, T.map_lo, T.ana_items, T.ana_off, T.ana_pieces, T.anf_items, T.anf_off, T.anf_pieces,
                     T.anf_og, T.anf_map_hi, T.anf_map_lo, T.smap_hi, T.smap_lo, T.tsyn_hi,
-                    T.tsyn_lo, T.tile_off, T.tile_info, T.syn_kt0, T.smap_hi_c2, T.smap_lo_c2, T.smap_hi_c4,
+                    T.tsyn_lo, T.tile_off, T.tile_info, T.smap_hi_c2, T.smap_lo_c2, T.smap_hi_c4,
                     T.smap_lo_c4};
     for (void* p : ptrs)
         if (p) cudaFree(p);
