@@ -1,5 +1,6 @@
-// Binary64 -> binary32 conversion, round to nearest, ties to even (IEEE 754
-// convertFormat), on the integer ALU.  GB300's FP64 pipe is narrow (a few
+// Conversions between binary64 and binary32 on the integer ALU: binary64 ->
+// binary32 rounds to nearest, ties to even (IEEE 754 convertFormat), and
+// binary32 -> binary64 is exact.  GB300's FP64 pipe is narrow (a few
 // operations per clock per SM), and a conversion instruction goes through
 // it: kernels that convert many FP64 inputs use this instead.
 //
@@ -55,6 +56,34 @@ SPH_HD float f64_to_f32_rn(double x) {
 #else
     float y;
     std::memcpy(&y, &f, sizeof y);
+    return y;
+#endif
+}
+
+// Binary32 -> binary64, exact, on the integer ALU: the exponent is rebiased
+// and the fraction widened.  Zeros are formed directly; binary32 subnormals,
+// infinities and NaNs take the compiler's own conversion.
+SPH_HD double f32_to_f64(float x) {
+    uint32_t u;
+#if defined(__CUDA_ARCH__)
+    u = __float_as_uint(x);
+#else
+    std::memcpy(&u, &x, sizeof u);
+#endif
+    const uint32_t e = (u >> 23) & 0xFFu;
+    uint64_t b;
+    if (e != 0u && e != 0xFFu) {
+        b = (uint64_t(u & 0x80000000u) << 32) | (uint64_t(e - 127u + 1023u) << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
+    } else if ((u & 0x7FFFFFFFu) == 0u) {
+        b = uint64_t(u) << 32;   // +-0
+    } else {
+        return static_cast<double>(x);
+    }
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double(static_cast<long long>(b));
+#else
+    double y;
+    std::memcpy(&y, &b, sizeof y);
     return y;
 #endif
 }

@@ -349,13 +349,30 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
             if (!*abort) {
                 for (int m = og.y; m < og.z; ++m) {
                     const int lo = m > 0 ? m : 1, pk = packed_off(N, m) - lo;
-                    for (int L = lo + ft; L <= N; L += 128) {
-                        const int pi = pk + L;
-                        const float* hL = sg + (ext_row(N, m, L) - og.x) * 2 * NF;
-                        const float* hU = sg + (ext_row(N, m, L + 1) - og.x) * 2 * NF;
-                        const float* hD = L - 1 >= m ? sg + (ext_row(N, m, L - 1) - og.x) * 2 * NF : nullptr;
-                        const double2 f = a.forcing ? a.forcing[pi] : make_double2(0.0, 0.0);
-                        a.out[pi] = finish32_entry(0, L, m, a.finc[pi], hL, hU, hD, a.alpha[pi], f, a.nu, a.omega_d);
+                    // four entries per thread at a time, their operands loaded
+                    // first: one load latency per four entries (the group's
+                    // finish is the CTA's tail after its last MMA)
+                    for (int L0 = lo + ft; L0 <= N; L0 += 4 * 128) {
+                        double2 al[4], fo[4];
+                        float4 fc[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int L = L0 + 128 * u, pi = pk + L;
+                            if (L <= N) {
+                                al[u] = a.alpha[pi];
+                                fc[u] = a.finc[pi];
+                                fo[u] = a.forcing ? a.forcing[pi] : make_double2(0.0, 0.0);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int L = L0 + 128 * u, pi = pk + L;
+                            if (L > N) break;
+                            const float* hL = sg + (ext_row(N, m, L) - og.x) * 2 * NF;
+                            const float* hU = sg + (ext_row(N, m, L + 1) - og.x) * 2 * NF;
+                            const float* hD = L - 1 >= m ? sg + (ext_row(N, m, L - 1) - og.x) * 2 * NF : nullptr;
+                            a.out[pi] = finish32_entry(0, L, m, fc[u], hL, hU, hD, al[u], fo[u], a.nu, a.omega_d);
+                        }
                     }
                 }
             }
@@ -1402,7 +1419,8 @@ static int tc_setup_analysis_fin(sphnse_plan* P) {
             g.items.push_back(make_int4(r0, 0, np, ncol | (kt0 << 16) | (bj << 24)));
             g.og.push_back(make_int4(row0, m, m1, r1 == row0 + rows ? 1 : 0));
             g.pcs.push_back(pc);
-            g.cost += (TC_TILE_M + 24 * np) * double(nch - kt0) / nch;
+            // a CTA's time follows its K-tile stages (eight MMAs each)
+            g.cost += double(nch - kt0);
         }
         groups.push_back(std::move(g));
         m = m1;

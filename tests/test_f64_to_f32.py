@@ -1,10 +1,11 @@
-"""The integer-ALU binary64 -> binary32 conversion of the device code
-(csrc/f64cvt.h, round to nearest, ties to even) against the host's own
-conversion (IEEE 754 round to nearest in the default rounding mode), bit for
-bit: random bit patterns over every exponent, and the boundaries where a
-mistake would show: ties with even and odd last bits, a carry out of the
-fraction, the largest finite value and overflow, the smallest normal value
-and the subnormal range, signed zeros, infinities and NaNs."""
+"""The integer-ALU conversions of the device code (csrc/f64cvt.h) against the
+host's own conversions, bit for bit. Binary64 -> binary32 (round to nearest,
+ties to even): random bit patterns over every exponent, and the boundaries
+where a mistake would show: ties with even and odd last bits, a carry out of
+the fraction, the largest finite value and overflow, the smallest normal
+value and the subnormal range, signed zeros, infinities and NaNs. Binary32 ->
+binary64 (exact): a stride through all 2^32 patterns and every exponent's
+boundary fractions."""
 import os
 import shutil
 import subprocess
@@ -55,8 +56,25 @@ int main() {
                               3.4028235677973362e38, 1e39, -1e39, 1.1754943508222875e-38, 1.1754942807573643e-38,
                               1.401298464324817e-45, 7.006492321624085e-46, 7.006492321624087e-46, 1e-50, 4.9e-324};
     for (double x : special) { uint64_t b; std::memcpy(&b, &x, 8); check(b); check(b ^ (1ull << 63)); }
-    std::printf("checked %ld mismatches %ld\n", n, bad);
-    return bad != 0;
+    // binary32 -> binary64 (exact): every 61st bit pattern, and every
+    // exponent with its boundary fractions
+    long bad2 = 0, n2 = 0;
+    auto check2 = [&](uint32_t u) {
+        float x; std::memcpy(&x, &u, 4);
+        const double a = sph::f32_to_f64(x), b = static_cast<double>(x);
+        uint64_t ua, ub; std::memcpy(&ua, &a, 8); std::memcpy(&ub, &b, 8);
+        ++n2;
+        if (std::isnan(b) ? !std::isnan(a) : ua != ub) {
+            if (bad2 < 10) std::printf("widen mismatch %08x: %016llx vs %016llx\n", u, (unsigned long long)ua, (unsigned long long)ub);
+            ++bad2;
+        }
+    };
+    for (uint64_t u = 0; u <= 0xFFFFFFFFull; u += 61) check2(uint32_t(u));
+    for (uint32_t e = 0; e < 256; ++e)
+        for (uint32_t fr : {0u, 1u, 0x400000u, 0x7FFFFFu})
+            for (uint32_t sg : {0u, 0x80000000u}) check2(sg | (e << 23) | fr);
+    std::printf("checked %ld mismatches %ld; widened %ld mismatches %ld\n", n, bad, n2, bad2);
+    return bad != 0 || bad2 != 0;
 }
 """
 
@@ -72,4 +90,4 @@ def test_integer_conversion_matches_ieee_round_to_nearest(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     print(r.stdout)
     assert r.returncode == 0, r.stdout
-    assert "mismatches 0" in r.stdout
+    assert "mismatches 0;" in r.stdout and r.stdout.strip().endswith("mismatches 0")
