@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
     uint64_t* acc_empty = b_full + 6;
     uint64_t* st_full = b_full + 8;                               // FIN: an order group's rows staged
     uint64_t* st_empty = st_full + 2;                             // FIN: its F written, buffer free
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(FIN ? st_empty + 2 : b_full + 8);
+    uint64_t* st_half = st_empty + 2;                             // FIN: the group's first order staged
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(FIN ? st_half + 2 : b_full + 8);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + 256);   // FIN: 2 x [srows][4]
 
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
             if constexpr (FIN) {
                 mbar_init(&st_full[b], 128);
                 mbar_init(&st_empty[b], 128);
+                mbar_init(&st_half[b], 128);
             }
         }
         *abort = 0;
@@ -328,10 +330,22 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
-            if (FIN && a.og[ib + i].w) {
-                mbar_arrive(&st_full[g & 1]);   // the group's rows are staged
-                ++g;
-                new_group = true;
+            if constexpr (FIN) {
+                // a group of two orders releases its first order's finish
+                // once that order's last row is staged (other groups with
+                // their last tile): the finish of a CTA's last group is
+                // its tail after the last MMA
+                const int4 og = a.og[ib + i];
+                const int end0 = ext_off(N, og.y + 1) - 1;
+                const bool first = og.z - og.y == 2
+                                       ? itm.x <= end0 && end0 < itm.x + 16 * (((itm.w >> 24) & 7) + 1)
+                                       : og.w != 0;
+                if (first) mbar_arrive(&st_half[g & 1]);
+                if (og.w) {
+                    mbar_arrive(&st_full[g & 1]);   // the group's rows are staged
+                    ++g;
+                    new_group = true;
+                }
             }
         }
     } else if constexpr (FIN) {
@@ -344,10 +358,15 @@ __global__ void __launch_bounds__(FIN ? 448 : 320, 1) k_ana_tc(TcAnaArgs a) {
         for (int i = 0; i < nI; ++i) {
             const int4 og = a.og[ib + i];
             if (!og.w) continue;
-            mbar_wait(&st_full[g & 1], (g >> 1) & 1, abort, a.status);
+            mbar_wait(&st_half[g & 1], (g >> 1) & 1, abort, a.status);
             const float* sg = stage + (g & 1) * a.srows * 2 * NF;
+            const bool two = og.z - og.y == 2;
+            if (!two) mbar_wait(&st_full[g & 1], (g >> 1) & 1, abort, a.status);
             if (!*abort) {
                 for (int m = og.y; m < og.z; ++m) {
+                    // the second order of a two-order group: all rows staged
+                    if (two && m > og.y) mbar_wait(&st_full[g & 1], (g >> 1) & 1, abort, a.status);
+                    if (*abort) break;
                     const int lo = m > 0 ? m : 1, pk = packed_off(N, m) - lo;
                     // four entries per thread at a time, their operands loaded
                     // first: one load latency per four entries (the group's
