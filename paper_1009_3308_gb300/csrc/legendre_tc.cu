@@ -1741,6 +1741,18 @@ int tc_batch_init(sphnse_plan* P, int nb, TcBatch* B, int ngmax, int nsmax, int 
         bins[bb].push_back(its[idx]);
         load[bb] += cost[idx];
     }
+    // within a CTA, long and short items alternate (LPT leaves the short
+    // ones last, where their epilogues and new tensor maps, not the table
+    // stream, would set the pace)
+    for (auto& bi : bins) {
+        std::vector<int4> alt;
+        alt.reserve(bi.size());
+        for (size_t lo = 0, hi = bi.size(); lo < hi;) {
+            alt.push_back(bi[lo++]);
+            if (lo < hi) alt.push_back(bi[--hi]);
+        }
+        bi.swap(alt);
+    }
     // every CTA's list at a fixed stride (padded with unused slots)
     size_t stride = 1;
     for (auto& bi : bins) stride = std::max(stride, bi.size());
