@@ -639,7 +639,7 @@ def main():
     # the dominant kernel's duration: an event pair around it on every
     # SAMPLE-th RHS of the timed region (a pair keeps the kernel from starting
     # early under its predecessor, so pairs on every call would slow the loop)
-    SAMPLE = 8
+    SAMPLE = 32   # ~94 samples in the default 3000 steps
     plan.set("TIMING_PERIOD", SAMPLE)
     lib.sphnse_stage_timing(plan.handle, 1 << dom_id)
     barrier(world)
