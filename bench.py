@@ -677,7 +677,7 @@ def main():
                 "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes": nbytes,
                 "table_entries": ent if ent else sizes(L, nlat)[2],
                 "avg_launch_ms": avg_ms, "timed_launches": stage[dom]["launches"],
-                "duration_sampling": f"CUDA events around every {SAMPLE}th launch in the timed region",
+                "duration_sampling": f"CUDA events around one launch in every {SAMPLE} in the timed region",
                 "traffic": ncu_traffic(f"{dom}:{prec}:L511")}
 
     # end to end through the C ABI with host buffers (sphnse_rhs_host): every
