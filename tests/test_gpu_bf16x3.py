@@ -155,6 +155,32 @@ def test_zero_state_gives_the_forcing_exactly(prec):
     np.testing.assert_array_equal(got, f)
 
 
+@pytest.mark.parametrize("prec,split", [("fp32", 0), ("bf16x3", 0), ("bf16x3", 1)])
+def test_forced_state_matches_oracle(prec, split):
+    """A nonzero state with a nonzero forcing on every coefficient (Eq.
+    (ode): F = fhat - nu lam alpha - N), with and without the split Coriolis
+    term (Eq. (Coriolis_ZLm)): the FP32 update adds the forcing in FP64, and
+    here both parts are of the same size. L = 63 on 96 x 192 (tensor-core
+    grid), against the FP64 oracle."""
+    from paper_1009_3308_gb300 import Plan
+    L, nlon, nu, Om = 63, 192, 1e-3, 1.0
+    prob = Problem(L, nlon, nu, Om)
+    a = coefficients(L, 777, 0.1) * 3.0
+    ref0 = rhs_separable(prob, a)
+    f = coefficients(L, 778, 0.1) * (np.linalg.norm(ref0) / np.linalg.norm(coefficients(L, 778, 0.1)))
+    ref = rhs_separable(prob, a, forcing=f)
+    plan = Plan(L, nlon // 2, nlon, nu, Om, precision=prec)
+    if split:
+        plan.set("CORIOLIS_SPLIT", 1)
+    got = plan.rhs(_dev(a), forcing=_dev(f)).cpu().numpy()
+    err = _rel(got, ref)
+    # the forcing itself passes unchanged: F - fhat against the unforced oracle
+    err0 = _rel(got - f, ref0)
+    print(f"{prec} split={split}: forced rel err {err:.2e}, unforced part {err0:.2e}")
+    assert err <= 3e-5 and err0 <= 3e-5, (err, err0)
+    assert plan.sync() == 0
+
+
 @pytest.mark.parametrize("L,nlon", [(5, 18), (127, 768)])
 def test_bf16x3_plan_off_the_tensor_core_grid(L, nlon):
     """A BF16X3 plan whose grid the tensor-core kernels do not take (odd
